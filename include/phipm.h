@@ -1,0 +1,167 @@
+/*
+ * phipm.h -- C ABI of the GB300 (sm_103a) phipm library.
+ *
+ * Computes u(t_end) = sum_{k=0}^{p} t_end^k phi_k(t_end A) b_k, the solution at
+ * t_end of u'(t) = A u + sum_{j=1}^{p} t^{j-1}/(j-1)! b_j, u(0) = b_0
+ * (Niesen & Wright, Sec. 3.3, Eqs. lincomb2 and phide), by the adaptive
+ * time-stepped Krylov method of Sec. 3 (Algorithms 3 and 4): each step builds
+ * the Krylov basis of A for w_p (Arnoldi, Algorithm 1, or Lanczos, Algorithm 2),
+ * exponentiates the augmented matrix of Eq. (hathm), applies the corrector of
+ * Eq. (phipapprox2), and lets the error estimate of Eq. (errest) adapt the step
+ * size tau and the Krylov dimension m (Sec. 3.4).  The call follows the paper's
+ * interface [u, stats] = phipm(t, A, b, tol, symm, m) of Sec. 3.5.
+ *
+ * Every step of the method runs in CUDA kernels on the device of the calling
+ * thread; there is no CPU fallback.  If the library cannot run on the GPU it
+ * returns PHIPM_ECUDA.
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as phipm_status codes; the library never traps or
+ *     aborts.  phipm_last_error(h) holds a message for the last failure.
+ *   - "device" pointers are CUDA global-memory pointers owned by the caller;
+ *     "host" pointers are ordinary host memory owned by the caller.
+ *   - Calls are ordered on the stream passed in (a cudaStream_t given as
+ *     void*; NULL is the legacy default stream).  A solve returns after one
+ *     stream synchronisation, so stats and status are final on return.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef PHIPM_H
+#define PHIPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PHIPM_OK = 0,
+  PHIPM_EINVAL = 1,       /* invalid argument (sizes, pointers, p, tol, operator) */
+  PHIPM_ENOMEM = 2,       /* device workspace allocation failed                    */
+  PHIPM_ECUDA = 3,        /* a CUDA call failed (no device, launch error, ...)     */
+  PHIPM_ENONFINITE = 4,   /* ten non-finite error estimates in a row               */
+  PHIPM_EMAXSTEPS = 5,    /* params.max_steps or params.max_rejects exceeded       */
+  PHIPM_ETIMEOUT = 6,     /* a bounded device-side wait gave up                    */
+  PHIPM_EBOUNDS = 7       /* a device-side bounds check failed                     */
+} phipm_status;
+
+typedef enum {
+  PHIPM_F64 = 0,          /* basis, SpMV and all vector work in FP64                     */
+  PHIPM_F32_MIXED = 1     /* basis and SpMV in FP32 with FP32 accumulation; Gram-Schmidt
+                             coefficients, norms, H, the exponential, eps and u in FP64   */
+} phipm_precision;
+
+typedef enum { PHIPM_OP_CSR = 0, PHIPM_OP_STENCIL = 1 } phipm_op_kind;
+
+/* CSR matrix, n x n.  rowptr[n+1], colind[nnz] (0-based, int32), values[nnz] (FP64).
+ * For phipm_solve*: device pointers.  For phipm_solve_host: host pointers. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* values;
+} phipm_csr;
+
+/* Constant-coefficient stencil on an nx x ny x nz grid of interior unknowns with
+ * homogeneous Dirichlet data, numbered i = x + nx*(y + ny*z) (x fastest):
+ *   (Ax)_i = c_center x_i + sum_{d<ndim} ( c_minus[d] x_{i-e_d} + c_plus[d] x_{i+e_d} ),
+ * with neighbours outside the grid dropped.  ndim = 1, 2 or 3; unused extents = 1. */
+typedef struct {
+  int32_t ndim, nx, ny, nz;
+  double c_center;
+  double c_minus[3];
+  double c_plus[3];
+} phipm_stencil;
+
+typedef struct {
+  int32_t kind;           /* phipm_op_kind */
+  phipm_csr csr;          /* used when kind == PHIPM_OP_CSR     */
+  phipm_stencil st;       /* used when kind == PHIPM_OP_STENCIL */
+} phipm_operator;
+
+/* stats(1..4) of Sec. 3.5 plus the sum of accepted error estimates.
+ * matvecs counts the products with A actually performed (the basis is reused
+ * when only tau changes and extended when m grows).  krylov_steps counts
+ * Arnoldi/Lanczos steps; gs_vectors sums, over classical Gram-Schmidt steps,
+ * the number of basis vectors each projection pass touched (j+1 at step j;
+ * 0 for Lanczos steps).  kernel_ms is the device time of the solver kernel,
+ * from CUDA events on the call's stream. */
+typedef struct {
+  int64_t steps;
+  int64_t rejects;
+  int64_t matvecs;
+  int64_t expms;
+  double err_est_sum;
+  int64_t krylov_steps;
+  int64_t gs_vectors;
+  double kernel_ms;
+} phipm_stats;
+
+/* Method parameters.  phipm_default_params() gives the paper's values:
+ * gamma = 0.8, delta = 1.2 (Sec. 3.4), m_init = 10 (Algorithm 3), m_max = 64,
+ * theta13 = 5.37 (Eq. 8), breakdown_tol = 1e-12 (relative to ||A||_inf). */
+typedef struct {
+  double gamma;
+  double delta;
+  int32_t m_init;
+  int32_t m_max;          /* 1 <= m_max <= PHIPM_M_MAX */
+  double theta13;
+  double breakdown_tol;
+  int64_t max_steps;
+  int64_t max_rejects;
+  int32_t precision;      /* phipm_precision */
+  int32_t controller;     /* 0 = the paper's controller; 1 = learned proposal (see below) */
+  int64_t timeout_cycles; /* bound on every device-side spin-wait, in clock64 cycles */
+} phipm_params;
+
+#define PHIPM_M_MAX 64
+#define PHIPM_P_MAX 8
+
+void phipm_default_params(phipm_params* out);
+
+typedef struct phipm_handle phipm_handle;
+
+/* Create a handle on the current CUDA device.  params may be NULL (defaults).
+ * The handle owns its device workspace (grown on demand, freed by destroy). */
+phipm_status phipm_create(phipm_handle** h, const phipm_params* params);
+void phipm_destroy(phipm_handle* h);
+const char* phipm_last_error(const phipm_handle* h);
+phipm_status phipm_set_params(phipm_handle* h, const phipm_params* params);
+
+/* Single problem, device buffers (Sec. 3.5 interface).
+ *   t_end  > 0, finite
+ *   A      operator; CSR arrays are device pointers
+ *   p      0 <= p <= PHIPM_P_MAX; b[0..p] are p+1 device pointers to n FP64 values
+ *   tol    absolute tolerance Tol of Eq. (taunew) on the 2-norm; <= 0 selects 1e-7
+ *   symm   1 symmetric (Lanczos), 0 not (Arnoldi), -1 detect on the device
+ *   u      device pointer to n FP64 values, written (may not alias any b[k])
+ *   stats  host pointer, may be NULL
+ *   stream cudaStream_t (as void*)
+ * The precision of the basis and SpMV is params.precision. */
+phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
+                         const double* const* b, double tol, int32_t symm, double* u,
+                         phipm_stats* stats, void* stream);
+
+/* Same computation with every array in host memory (CSR arrays, b[k], u):
+ * copies the operator and b to the device, solves, and copies u back. */
+phipm_status phipm_solve_host(phipm_handle* h, double t_end, const phipm_operator* A_host,
+                              int32_t p, const double* const* b_host, double tol, int32_t symm,
+                              double* u_host, phipm_stats* stats, void* stream);
+
+/* Batched: count independent problems in one persistent launch.  Arrays of
+ * length count in host memory: t_end, A (CSR arrays device pointers), p, b
+ * (b[i] is a host array of p[i]+1 device pointers), tol, symm, u (device
+ * pointers).  stats and per_problem (host, may be NULL) receive one entry per
+ * problem.  Returns PHIPM_OK only if every problem succeeded. */
+phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, const double* t_end,
+                                 const phipm_operator* A, const int32_t* p,
+                                 const double* const* const* b, const double* tol,
+                                 const int32_t* symm, double* const* u, phipm_stats* stats,
+                                 phipm_status* per_problem, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHIPM_H */

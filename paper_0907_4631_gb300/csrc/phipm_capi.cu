@@ -1,0 +1,601 @@
+// Host side of the C ABI declared in include/phipm.h, and the kernels that
+// run the device engine (phipm_engine.cuh):
+//   k_solve_grid     one problem, every CTA of a cooperative launch;
+//   k_solve_queue    a persistent CTA per slot that pulls problems from an
+//                    atomic queue (batched form, and single small problems).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "phipm.h"
+#include "phipm_engine.cuh"
+
+// ------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------
+template <class S>
+__global__ void __launch_bounds__(PM_THREADS, 1)
+k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char pm_smem[];
+  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
+  GridTeam team{bar, err, prm.timeout_cycles};
+  phipm_device<GridTeam, S>(team, P, prm, *res, s, w, w.expm);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int e = *((volatile int*)err);
+    if (e != 0 && res->status == PM_OK) res->status = e;
+  }
+}
+
+// Workspace of one queue slot (one CTA): V, W, Y and the exponential scratch.
+struct SlotLayout {
+  long long ld;          // vector stride (elements)
+  long long v_off, w_off, y_off, e_off;   // byte offsets inside the slot
+  long long bytes;       // bytes per slot
+};
+
+template <class S>
+__global__ void __launch_bounds__(PM_THREADS, 1)
+k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams prm, DevResult* res,
+              unsigned char* slots, SlotLayout lay, int* queue) {
+  extern __shared__ __align__(16) unsigned char pm_smem[];
+  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
+  __shared__ int s_next;
+  unsigned char* base = slots + (size_t)blockIdx.x * lay.bytes;
+  CtaTeam team;
+  PmWork w{nullptr, nullptr, (double*)(base + lay.e_off)};
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int q = s_next;
+    __syncthreads();
+    if (q >= count) break;
+    const int id = order[q];
+    DevProblem P = probs[id];
+    P.V = base + lay.v_off;
+    P.W = (double*)(base + lay.w_off);
+    P.Y = base + lay.y_off;
+    P.ld = lay.ld;
+    phipm_device<CtaTeam, S>(team, P, prm, res[id], s, w, w.expm);
+    __syncthreads();
+  }
+}
+
+// FP32 copy of CSR values for the FP32 basis mode
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------------------------
+// handle
+// ------------------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool ensure(size_t bytes) {
+    if (bytes <= cap) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max(bytes, (size_t)256);
+    if (cudaMalloc(&p, want) != cudaSuccess) { p = nullptr; return false; }
+    cap = want;
+    return true;
+  }
+  void release() { if (p) cudaFree(p); p = nullptr; cap = 0; }
+};
+
+struct HostBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool ensure(size_t bytes) {
+    if (bytes <= cap) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&p, std::max(bytes, (size_t)256)) != cudaSuccess) { p = nullptr; return false; }
+    cap = std::max(bytes, (size_t)256);
+    return true;
+  }
+  void release() { if (p) cudaFreeHost(p); p = nullptr; cap = 0; }
+};
+
+struct phipm_handle {
+  int device = 0;
+  int num_sms = 0;
+  phipm_params params;
+  std::string err;
+  DevBuf ws;          // V, W, Y of the grid solve / queue slots
+  DevBuf sync;        // barrier words + error flag + queue counter
+  DevBuf partials, phi_g, expm, valf, res, probs, order;
+  DevBuf h_rowptr, h_colind, h_vals, h_b, h_u;   // device staging for phipm_solve_host
+  HostBuf res_host, probs_host, order_host;
+  int grid_blocks[2] = {0, 0};   // cooperative grid size per precision
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the solver kernel
+};
+
+static phipm_status fail(phipm_handle* h, phipm_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+static phipm_status cuda_fail(phipm_handle* h, cudaError_t e, const char* what) {
+  return fail(h, PHIPM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" void phipm_default_params(phipm_params* o) {
+  if (!o) return;
+  o->gamma = 0.8;
+  o->delta = 1.2;
+  o->m_init = 10;
+  o->m_max = 64;
+  o->theta13 = 5.37;
+  o->breakdown_tol = 1e-12;
+  o->max_steps = 1000000;
+  o->max_rejects = 1000000;
+  o->precision = PHIPM_F64;
+  o->controller = 0;
+  o->timeout_cycles = 20000000000ll;   // ~10 s at 2 GHz
+}
+
+static bool params_ok(const phipm_params& p, std::string& why) {
+  if (!(p.gamma > 0 && p.gamma < p.delta)) { why = "need 0 < gamma < delta"; return false; }
+  if (p.m_max < 1 || p.m_max > PHIPM_M_MAX) { why = "m_max out of [1, 64]"; return false; }
+  if (p.m_init < 1 || p.m_init > p.m_max) { why = "m_init out of [1, m_max]"; return false; }
+  if (!(p.theta13 > 0)) { why = "theta13 must be positive"; return false; }
+  if (!(p.breakdown_tol >= 0)) { why = "breakdown_tol must be >= 0"; return false; }
+  if (p.precision != PHIPM_F64 && p.precision != PHIPM_F32_MIXED) { why = "unknown precision"; return false; }
+  if (p.controller != 0 && p.controller != 1) { why = "unknown controller"; return false; }
+  if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
+  return true;
+}
+
+extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* params) {
+  if (!out) return PHIPM_EINVAL;
+  *out = nullptr;
+  phipm_handle* h = new phipm_handle();
+  phipm_default_params(&h->params);
+  if (params) {
+    std::string why;
+    if (!params_ok(*params, why)) { delete h; return PHIPM_EINVAL; }
+    h->params = *params;
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { delete h; return PHIPM_ECUDA; }
+  e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { delete h; return PHIPM_ECUDA; }
+  int smem = (int)sizeof(PmShared);
+  if (cudaFuncSetAttribute(k_solve_grid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_grid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_queue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_solve_queue<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    delete h;
+    return PHIPM_ECUDA;
+  }
+  int occ0 = 0, occ1 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_solve_grid<double>, PM_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_solve_grid<float>, PM_THREADS, smem);
+  h->grid_blocks[0] = std::max(1, occ0) * h->num_sms;
+  h->grid_blocks[1] = std::max(1, occ1) * h->num_sms;
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    delete h;
+    return PHIPM_ECUDA;
+  }
+  if (!h->sync.ensure(4096) || !h->res.ensure(sizeof(DevResult)) || !h->res_host.ensure(sizeof(DevResult)) ||
+      !h->phi_g.ensure(2 * 2 * PM_NA * sizeof(double)) || !h->expm.ensure(9 * PM_NA2 * sizeof(double))) {
+    delete h;
+    return PHIPM_ENOMEM;
+  }
+  *out = h;
+  return PHIPM_OK;
+}
+
+extern "C" void phipm_destroy(phipm_handle* h) {
+  if (!h) return;
+  DevBuf* bufs[] = {&h->ws, &h->sync, &h->partials, &h->phi_g, &h->expm, &h->valf, &h->res, &h->probs,
+                    &h->order, &h->h_rowptr, &h->h_colind, &h->h_vals, &h->h_b, &h->h_u};
+  for (DevBuf* b : bufs) b->release();
+  h->res_host.release();
+  h->probs_host.release();
+  h->order_host.release();
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+extern "C" const char* phipm_last_error(const phipm_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" phipm_status phipm_set_params(phipm_handle* h, const phipm_params* params) {
+  if (!h || !params) return PHIPM_EINVAL;
+  std::string why;
+  if (!params_ok(*params, why)) return fail(h, PHIPM_EINVAL, why);
+  h->params = *params;
+  return PHIPM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------
+static DevParams make_params(const phipm_params& p) {
+  DevParams d;
+  d.gamma = p.gamma;
+  d.delta = p.delta;
+  d.theta13 = p.theta13;
+  d.breakdown_tol = p.breakdown_tol;
+  d.m_init = p.m_init;
+  d.m_max = p.m_max;
+  d.max_steps = p.max_steps;
+  d.max_rejects = p.max_rejects;
+  d.timeout_cycles = p.timeout_cycles;
+  // [13/13] Pade coefficients of e^x, c_j = (26-j)! 13! / (26! j! (13-j)!), from their closed form
+  double c = 1.0;
+  for (int j = 0; j <= 13; ++j) {
+    d.pade_b[j] = c;
+    c = c * (double)(13 - j) / ((double)(26 - j) * (double)(j + 1));
+  }
+  return d;
+}
+
+static phipm_status check_operator(phipm_handle* h, const phipm_operator* A, long long& nnz_model) {
+  if (!A) return fail(h, PHIPM_EINVAL, "operator is NULL");
+  if (A->kind == PHIPM_OP_CSR) {
+    if (A->csr.n < 0 || A->csr.nnz < 0) return fail(h, PHIPM_EINVAL, "negative CSR sizes");
+    if (A->csr.n > 0 && (!A->csr.rowptr || (A->csr.nnz > 0 && (!A->csr.colind || !A->csr.values))))
+      return fail(h, PHIPM_EINVAL, "CSR arrays missing");
+    nnz_model = A->csr.nnz;
+    return PHIPM_OK;
+  }
+  if (A->kind == PHIPM_OP_STENCIL) {
+    const phipm_stencil& st = A->st;
+    if (st.ndim < 1 || st.ndim > 3) return fail(h, PHIPM_EINVAL, "stencil ndim must be 1, 2 or 3");
+    if (st.nx < 1 || st.ny < 1 || st.nz < 1) return fail(h, PHIPM_EINVAL, "stencil extents must be >= 1");
+    if ((st.ndim < 2 && st.ny != 1) || (st.ndim < 3 && st.nz != 1)) return fail(h, PHIPM_EINVAL, "unused stencil extents must be 1");
+    const long long n = (long long)st.nx * st.ny * st.nz;
+    if (n > 0x7fffffffll) return fail(h, PHIPM_EINVAL, "stencil too large for int32 indexing");
+    const long long dims[3] = {st.nx, st.ny, st.nz};
+    nnz_model = n;
+    for (int d = 0; d < st.ndim; ++d) nnz_model += 2 * (n / dims[d]) * (dims[d] - 1);
+    return PHIPM_OK;
+  }
+  return fail(h, PHIPM_EINVAL, "unknown operator kind");
+}
+
+static int op_n(const phipm_operator* A) {
+  return A->kind == PHIPM_OP_CSR ? A->csr.n : A->st.nx * A->st.ny * A->st.nz;
+}
+
+static DevOp make_devop(const phipm_operator* A, long long nnz_model, const float* valf) {
+  DevOp o;
+  memset(&o, 0, sizeof(o));
+  o.kind = A->kind == PHIPM_OP_CSR ? 0 : 1;
+  o.n = op_n(A);
+  o.nnz = nnz_model;
+  if (o.kind == 0) {
+    o.rowptr = A->csr.rowptr;
+    o.colind = A->csr.colind;
+    o.val = A->csr.values;
+    o.valf = valf;
+    o.ndim = 0;
+  } else {
+    o.ndim = A->st.ndim;
+    o.nx = A->st.nx;
+    o.ny = A->st.ny;
+    o.nz = A->st.nz;
+    o.cc = A->st.c_center;
+    for (int d = 0; d < 3; ++d) { o.cm[d] = A->st.c_minus[d]; o.cp[d] = A->st.c_plus[d]; }
+  }
+  return o;
+}
+
+static long long round_ld(long long n) { return std::max(64ll, (n + 63) & ~63ll); }
+
+static phipm_status map_status(int s) {
+  switch (s) {
+    case PM_OK: return PHIPM_OK;
+    case PM_EINVAL: return PHIPM_EINVAL;
+    case PM_ENONFINITE: return PHIPM_ENONFINITE;
+    case PM_EMAXSTEPS: return PHIPM_EMAXSTEPS;
+    case PM_ETIMEOUT: return PHIPM_ETIMEOUT;
+    case PM_EBOUNDS: return PHIPM_EBOUNDS;
+    default: return PHIPM_ECUDA;
+  }
+}
+
+static const char* status_text(phipm_status s) {
+  switch (s) {
+    case PHIPM_OK: return "ok";
+    case PHIPM_EINVAL: return "invalid argument";
+    case PHIPM_ENOMEM: return "out of device memory";
+    case PHIPM_ECUDA: return "CUDA error";
+    case PHIPM_ENONFINITE: return "ten non-finite error estimates in a row";
+    case PHIPM_EMAXSTEPS: return "step or reject limit exceeded";
+    case PHIPM_ETIMEOUT: return "a device-side wait timed out";
+    case PHIPM_EBOUNDS: return "device bounds check failed";
+  }
+  return "unknown";
+}
+
+static void fill_stats(phipm_stats* o, const DevResult& r, float kernel_ms) {
+  o->steps = r.steps;
+  o->rejects = r.rejects;
+  o->matvecs = r.matvecs;
+  o->expms = r.expms;
+  o->err_est_sum = r.err_est_sum;
+  o->krylov_steps = r.kry_steps;
+  o->gs_vectors = r.gs_vectors;
+  o->kernel_ms = kernel_ms;
+}
+
+// Problems up to this size run on one CTA; larger ones on the whole GPU.
+static const int kGridMinN = 16384;
+
+// ------------------------------------------------------------------------------------
+// single solve
+// ------------------------------------------------------------------------------------
+extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
+                                   const double* const* b, double tol, int32_t symm, double* u,
+                                   phipm_stats* stats, void* stream_) {
+  if (!h) return PHIPM_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  long long nnz_model = 0;
+  phipm_status st = check_operator(h, A, nnz_model);
+  if (st != PHIPM_OK) return st;
+  if (!(t_end > 0) || !std::isfinite(t_end)) return fail(h, PHIPM_EINVAL, "t_end must be positive and finite");
+  if (p < 0 || p > PHIPM_P_MAX) return fail(h, PHIPM_EINVAL, "p out of [0, 8]");
+  if (!std::isfinite(tol)) return fail(h, PHIPM_EINVAL, "tol must be finite");
+  if (symm < -1 || symm > 1) return fail(h, PHIPM_EINVAL, "symm must be -1, 0 or 1");
+  const int n = op_n(A);
+  if (n > 0 && (!b || !u)) return fail(h, PHIPM_EINVAL, "b or u is NULL");
+  for (int k = 0; k <= p && n > 0; ++k)
+    if (!b[k]) return fail(h, PHIPM_EINVAL, "b[k] is NULL");
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (n == 0) return PHIPM_OK;
+
+  const bool f32 = h->params.precision == PHIPM_F32_MIXED;
+  const size_t es = f32 ? 4 : 8;
+  const float* valf = nullptr;
+  cudaError_t e;
+  if (f32 && A->kind == PHIPM_OP_CSR && A->csr.nnz > 0) {
+    if (!h->valf.ensure((size_t)A->csr.nnz * 4)) return fail(h, PHIPM_ENOMEM, "valf");
+    k_to_float<<<std::min(4 * h->num_sms, (int)((A->csr.nnz + 255) / 256)), 256, 0, stream>>>(
+        A->csr.values, (float*)h->valf.p, A->csr.nnz);
+    valf = (const float*)h->valf.p;
+  }
+  DevProblem P;
+  memset(&P, 0, sizeof(P));
+  P.A = make_devop(A, nnz_model, valf);
+  P.p = p;
+  P.symm = symm;
+  P.t_end = t_end;
+  P.tol = tol;
+  for (int k = 0; k <= p; ++k) P.b[k] = b[k];
+  P.u = u;
+  const DevParams prm = make_params(h->params);
+  const int M1 = h->params.m_max + 1;
+  DevResult* res_h = (DevResult*)h->res_host.p;
+
+  if (n >= kGridMinN) {
+    const long long ld = round_ld(n);
+    const size_t vbytes = (size_t)M1 * ld * es, wbytes = (size_t)std::max(p, 1) * ld * 8, ybytes = 2 * (size_t)ld * es;
+    if (!h->ws.ensure(vbytes + wbytes + ybytes)) return fail(h, PHIPM_ENOMEM, "workspace");
+    P.V = h->ws.p;
+    P.W = (double*)((char*)h->ws.p + vbytes);
+    P.Y = (char*)h->ws.p + vbytes + wbytes;
+    P.ld = ld;
+    const int G = h->grid_blocks[f32 ? 1 : 0];
+    if (!h->partials.ensure((size_t)2 * G * PM_NSLOT * sizeof(double))) return fail(h, PHIPM_ENOMEM, "partials");
+    PmWork w{(double*)h->partials.p, (double*)h->phi_g.p, (double*)h->expm.p};
+    unsigned* bar = (unsigned*)h->sync.p;
+    int* err = (int*)((char*)h->sync.p + 1024);
+    DevResult* res_d = (DevResult*)h->res.p;
+    if ((e = cudaMemsetAsync(h->sync.p, 0, 2048, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
+    if ((e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
+    void* args[] = {(void*)&P, (void*)&prm, (void*)&res_d, (void*)&w, (void*)&bar, (void*)&err};
+    cudaEventRecord(h->ev0, stream);
+    e = cudaLaunchCooperativeKernel(f32 ? (const void*)k_solve_grid<float> : (const void*)k_solve_grid<double>,
+                                    dim3(G), dim3(PM_THREADS), args, sizeof(PmShared), stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch");
+    cudaEventRecord(h->ev1, stream);
+    if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(h, e, "result copy");
+  } else {
+    SlotLayout lay;
+    lay.ld = round_ld(n);
+    lay.v_off = 0;
+    lay.w_off = (long long)M1 * lay.ld * es;
+    lay.y_off = lay.w_off + (long long)std::max(p, 1) * lay.ld * 8;
+    lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
+    lay.e_off = (lay.e_off + 255) & ~255ll;
+    lay.bytes = lay.e_off + 9ll * PM_NA2 * 8;
+    if (!h->ws.ensure((size_t)lay.bytes)) return fail(h, PHIPM_ENOMEM, "workspace");
+    if (!h->probs.ensure(sizeof(DevProblem)) || !h->order.ensure(sizeof(int)) ||
+        !h->probs_host.ensure(sizeof(DevProblem) + sizeof(int)))
+      return fail(h, PHIPM_ENOMEM, "descriptors");
+    memcpy(h->probs_host.p, &P, sizeof(P));
+    int zero = 0;
+    memcpy((char*)h->probs_host.p + sizeof(DevProblem), &zero, sizeof(int));
+    int* queue = (int*)((char*)h->sync.p + 2048);
+    DevResult* res_d = (DevResult*)h->res.p;
+    if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, sizeof(DevProblem), cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + sizeof(DevProblem), sizeof(int), cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(queue, 0, sizeof(int), stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess)
+      return cuda_fail(h, e, "descriptor upload");
+    cudaEventRecord(h->ev0, stream);
+    if (f32)
+      k_solve_queue<float><<<1, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm,
+                                                                        res_d, (unsigned char*)h->ws.p, lay, queue);
+    else
+      k_solve_queue<double><<<1, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm,
+                                                                         res_d, (unsigned char*)h->ws.p, lay, queue);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "launch");
+    cudaEventRecord(h->ev1, stream);
+    if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(h, e, "result copy");
+  }
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (stats) {
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, h->ev0, h->ev1);
+    fill_stats(stats, *res_h, kms);
+  }
+  st = map_status(res_h->status);
+  if (st != PHIPM_OK) return fail(h, st, status_text(st));
+  return PHIPM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// host-buffer solve: H2D of the operator and b, device solve, D2H of u
+// ------------------------------------------------------------------------------------
+extern "C" phipm_status phipm_solve_host(phipm_handle* h, double t_end, const phipm_operator* A_host, int32_t p,
+                                        const double* const* b_host, double tol, int32_t symm, double* u_host,
+                                        phipm_stats* stats, void* stream_) {
+  if (!h) return PHIPM_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  long long nnz_model = 0;
+  phipm_status st = check_operator(h, A_host, nnz_model);
+  if (st != PHIPM_OK) return st;
+  if (p < 0 || p > PHIPM_P_MAX) return fail(h, PHIPM_EINVAL, "p out of [0, 8]");
+  const int n = op_n(A_host);
+  if (n > 0 && (!b_host || !u_host)) return fail(h, PHIPM_EINVAL, "b or u is NULL");
+  phipm_operator Ad = *A_host;
+  cudaError_t e;
+  if (A_host->kind == PHIPM_OP_CSR && n > 0) {
+    const long long nnz = A_host->csr.nnz;
+    if (!h->h_rowptr.ensure((size_t)(n + 1) * 4) || !h->h_colind.ensure((size_t)std::max(nnz, 1ll) * 4) ||
+        !h->h_vals.ensure((size_t)std::max(nnz, 1ll) * 8))
+      return fail(h, PHIPM_ENOMEM, "operator staging");
+    if ((e = cudaMemcpyAsync(h->h_rowptr.p, A_host->csr.rowptr, (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (nnz > 0 && (e = cudaMemcpyAsync(h->h_colind.p, A_host->csr.colind, (size_t)nnz * 4, cudaMemcpyHostToDevice, stream)) != cudaSuccess) ||
+        (nnz > 0 && (e = cudaMemcpyAsync(h->h_vals.p, A_host->csr.values, (size_t)nnz * 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess))
+      return cuda_fail(h, e, "operator upload");
+    Ad.csr.rowptr = (const int32_t*)h->h_rowptr.p;
+    Ad.csr.colind = (const int32_t*)h->h_colind.p;
+    Ad.csr.values = (const double*)h->h_vals.p;
+  }
+  const size_t vb = (size_t)std::max(n, 1) * 8;
+  if (!h->h_b.ensure(vb * (p + 1)) || !h->h_u.ensure(vb)) return fail(h, PHIPM_ENOMEM, "vector staging");
+  const double* bd[PHIPM_P_MAX + 1];
+  for (int k = 0; k <= p; ++k) {
+    bd[k] = (const double*)((char*)h->h_b.p + vb * k);
+    if (n > 0) {
+      if (!b_host[k]) return fail(h, PHIPM_EINVAL, "b[k] is NULL");
+      if ((e = cudaMemcpyAsync((void*)bd[k], b_host[k], (size_t)n * 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(h, e, "b upload");
+    }
+  }
+  st = phipm_solve(h, t_end, &Ad, p, bd, tol, symm, (double*)h->h_u.p, stats, stream_);
+  if (st != PHIPM_OK) return st;
+  if (n > 0) {
+    if ((e = cudaMemcpyAsync(u_host, h->h_u.p, (size_t)n * 8, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(h, e, "u download");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "u download");
+  }
+  return PHIPM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// batched: one persistent launch, one CTA per problem at a time, largest first
+// ------------------------------------------------------------------------------------
+extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, const double* t_end,
+                                           const phipm_operator* A, const int32_t* p,
+                                           const double* const* const* b, const double* tol,
+                                           const int32_t* symm, double* const* u, phipm_stats* stats,
+                                           phipm_status* per_problem, void* stream_) {
+  if (!h) return PHIPM_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (count < 0) return fail(h, PHIPM_EINVAL, "count < 0");
+  if (count == 0) return PHIPM_OK;
+  if (!t_end || !A || !p || !b || !tol || !symm || !u) return fail(h, PHIPM_EINVAL, "NULL array argument");
+  const bool f32 = h->params.precision == PHIPM_F32_MIXED;
+  if (f32) {
+    for (int i = 0; i < count; ++i)
+      if (A[i].kind == PHIPM_OP_CSR) return fail(h, PHIPM_EINVAL, "batched FP32 mode takes stencil operators");
+  }
+  const size_t es = f32 ? 4 : 8;
+  std::vector<DevProblem> probs(count);
+  std::vector<double> cost(count);
+  int nmax = 1, pmax = 1;
+  for (int i = 0; i < count; ++i) {
+    long long nnz_model = 0;
+    phipm_status st = check_operator(h, &A[i], nnz_model);
+    if (st != PHIPM_OK) return st;
+    if (!(t_end[i] > 0) || !std::isfinite(t_end[i])) return fail(h, PHIPM_EINVAL, "t_end must be positive and finite");
+    if (p[i] < 0 || p[i] > PHIPM_P_MAX) return fail(h, PHIPM_EINVAL, "p out of [0, 8]");
+    if (symm[i] < -1 || symm[i] > 1) return fail(h, PHIPM_EINVAL, "symm must be -1, 0 or 1");
+    const int n = op_n(&A[i]);
+    if (n > 0 && (!b[i] || !u[i])) return fail(h, PHIPM_EINVAL, "b[i] or u[i] is NULL");
+    DevProblem& P = probs[i];
+    memset(&P, 0, sizeof(P));
+    P.A = make_devop(&A[i], nnz_model, nullptr);
+    P.p = p[i];
+    P.symm = symm[i];
+    P.t_end = t_end[i];
+    P.tol = tol[i];
+    for (int k = 0; k <= p[i]; ++k) {
+      if (n > 0 && !b[i][k]) return fail(h, PHIPM_EINVAL, "b[i][k] is NULL");
+      P.b[k] = b[i][k];
+    }
+    P.u = u[i];
+    nmax = std::max(nmax, n);
+    pmax = std::max(pmax, (int)p[i]);
+    cost[i] = (double)n * (double)(nnz_model + 1) / std::max(1, n);
+  }
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  const int M1 = h->params.m_max + 1;
+  SlotLayout lay;
+  lay.ld = round_ld(nmax);
+  lay.v_off = 0;
+  lay.w_off = (long long)M1 * lay.ld * es;
+  lay.y_off = lay.w_off + (long long)pmax * lay.ld * 8;
+  lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
+  lay.e_off = (lay.e_off + 255) & ~255ll;
+  lay.bytes = lay.e_off + 9ll * PM_NA2 * 8;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f32 ? (const void*)k_solve_queue<float> : (const void*)k_solve_queue<double>,
+                                                PM_THREADS, sizeof(PmShared));
+  const int slots = std::max(1, std::min(count, std::max(1, occ) * h->num_sms));
+  if (!h->ws.ensure((size_t)lay.bytes * slots)) return fail(h, PHIPM_ENOMEM, "workspace");
+  const size_t pb = sizeof(DevProblem) * count, ob = sizeof(int) * count, rb = sizeof(DevResult) * count;
+  if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(pb + ob) ||
+      !h->res_host.ensure(rb))
+    return fail(h, PHIPM_ENOMEM, "descriptors");
+  memcpy(h->probs_host.p, probs.data(), pb);
+  memcpy((char*)h->probs_host.p + pb, order.data(), ob);
+  const DevParams prm = make_params(h->params);
+  int* queue = (int*)((char*)h->sync.p + 2048);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, pb, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + pb, ob, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(queue, 0, sizeof(int), stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(h->res.p, 0, rb, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "descriptor upload");
+  cudaEventRecord(h->ev0, stream);
+  if (f32)
+    k_solve_queue<float><<<slots, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, count,
+                                                                          prm, (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+  else
+    k_solve_queue<double><<<slots, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, count,
+                                                                           prm, (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "launch");
+  cudaEventRecord(h->ev1, stream);
+  if ((e = cudaMemcpyAsync(h->res_host.p, h->res.p, rb, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "result copy");
+  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "batched solve");
+  float kms = 0.f;
+  cudaEventElapsedTime(&kms, h->ev0, h->ev1);
+  const DevResult* rh = (const DevResult*)h->res_host.p;
+  phipm_status overall = PHIPM_OK;
+  for (int i = 0; i < count; ++i) {
+    const phipm_status si = map_status(rh[i].status);
+    if (per_problem) per_problem[i] = si;
+    if (stats) fill_stats(&stats[i], rh[i], kms);
+    if (si != PHIPM_OK && overall == PHIPM_OK) overall = si;
+  }
+  if (overall != PHIPM_OK) return fail(h, overall, status_text(overall));
+  return PHIPM_OK;
+}

@@ -1,0 +1,168 @@
+// Shared device-side definitions of the phipm engine: problem descriptors,
+// teams (who cooperates on one problem), bounded barriers and reductions,
+// and the float-pair arithmetic used to accumulate FP32 products at FP64
+// accuracy on the FP32 pipe.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define PM_MAXM 64
+#define PM_MAXP 8
+#define PM_NA (PM_MAXM + PM_MAXP + 1)   // largest augmented matrix, Eq. (hathm) + 1
+#define PM_NA2 (PM_NA * PM_NA)
+#define PM_THREADS 512
+#define PM_WARPS (PM_THREADS / 32)
+#define PM_NSLOT 66                     // partial sums per reduction (j+1 <= 65, +1)
+
+// status codes (mirror phipm_status in include/phipm.h)
+#define PM_OK 0
+#define PM_EINVAL 1
+#define PM_ENONFINITE 4
+#define PM_EMAXSTEPS 5
+#define PM_ETIMEOUT 6
+#define PM_EBOUNDS 7
+
+struct DevOp {
+  int kind;          // 0 CSR, 1 stencil
+  int n;
+  long long nnz;     // structural nonzeros (cost model, Eq. 4)
+  const int* rowptr;
+  const int* colind;
+  const double* val;     // CSR values, FP64 (caller's)
+  const float* valf;     // CSR values, FP32 copy (workspace; FP32 mode)
+  int ndim, nx, ny, nz;
+  double cc, cm[3], cp[3];
+};
+
+struct DevParams {
+  double gamma, delta, theta13, breakdown_tol;
+  int m_init, m_max;
+  long long max_steps, max_rejects;
+  long long timeout_cycles;
+  double pade_b[14];     // degree-13 Pade coefficients, computed on the host from their closed form
+};
+
+struct DevProblem {
+  DevOp A;
+  int p;
+  int symm;              // -1 detect, 0, 1
+  double t_end, tol;
+  const double* b[PM_MAXP + 1];
+  double* u;             // current solution u(t_k) = w_0, FP64, caller's buffer
+  // workspace (device)
+  void* V;               // (m_max+1) basis vectors of length ld, element type S
+  double* W;             // w_1..w_p, FP64, length ld each
+  void* Y;               // 2 buffers of length ld (unnormalised Krylov vector), type S
+  long long ld;
+};
+
+struct DevResult {
+  int status;
+  int symmetric;
+  long long steps, rejects, matvecs, expms;
+  long long kry_steps, gs_vectors;
+  double err_est_sum;
+  double normA, normb;
+  double last_tau;
+  int last_m;
+  int pad;
+};
+
+// ------------------------------------------------------------------------------------
+// bounded waits
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned pm_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier over G CTAs of a cooperative launch.  bar[0] = arrival count,
+// bar[32] = generation.  The spin is bounded by timeout cycles; on expiry the
+// error word is set and every later barrier returns at once.
+__device__ __forceinline__ bool pm_grid_barrier(unsigned* bar, int G, int* err, long long timeout) {
+  __syncthreads();
+  __shared__ int s_fail;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    unsigned* count = bar;
+    unsigned* gen = bar + 32;
+    unsigned g = pm_ld_acquire(gen);
+    __threadfence();
+    unsigned prev = atomicAdd(count, 1u);
+    if (prev == (unsigned)G - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      long long t0 = clock64();
+      while (pm_ld_acquire(gen) == g) {
+        if (*((volatile int*)err) != 0) { s_fail = 1; break; }
+        if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_fail = 1; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_fail == 0;
+}
+
+// A team is the set of CTAs that work on one problem.
+struct GridTeam {
+  unsigned* bar;
+  int* err;
+  long long timeout;
+  __device__ int rank() const { return blockIdx.x; }
+  __device__ int size() const { return gridDim.x; }
+  __device__ bool sync() const { return pm_grid_barrier(bar, gridDim.x, err, timeout); }
+  static constexpr bool multi = true;
+};
+
+struct CtaTeam {
+  __device__ int rank() const { return 0; }
+  __device__ int size() const { return 1; }
+  __device__ bool sync() const { __syncthreads(); return true; }
+  static constexpr bool multi = false;
+};
+
+// ------------------------------------------------------------------------------------
+// float-pair ("double-float") accumulation: exact FP32 products summed with
+// two-sum (Knuth) into an unevaluated hi+lo pair; about 44 significant bits.
+// ------------------------------------------------------------------------------------
+struct F2Acc {
+  float hi, lo;
+};
+__device__ __forceinline__ void f2_add_prod(F2Acc& a, float x, float y) {
+  float p = x * y;
+  float e = fmaf(x, y, -p);          // x*y = p + e exactly
+  float s = a.hi + p;
+  float z = s - a.hi;
+  float t = (a.hi - (s - z)) + (p - z);
+  a.lo += t + e;
+  a.hi = s;
+}
+__device__ __forceinline__ double f2_value(const F2Acc& a) { return (double)a.hi + (double)a.lo; }
+
+// ------------------------------------------------------------------------------------
+// reductions
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double pm_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double pm_warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Rows owned by CTA r of a team of G CTAs for a vector of length n.
+__device__ __forceinline__ void pm_rows(int n, int r, int G, int& lo, int& hi) {
+  long long chunk = ((long long)n + G - 1) / G;
+  chunk = (chunk + 63) & ~63ll;
+  long long a = chunk * r, b = a + chunk;
+  lo = (int)(a < n ? a : n);
+  hi = (int)(b < n ? b : n);
+}

@@ -1,0 +1,259 @@
+"""Python binding of libphipm (include/phipm.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module turns
+torch tensors (device memory, streams) and numpy arrays into the plain
+pointers and sizes of the C ABI.  If the library is missing or cannot load, the
+import of the native library raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS = range(8)
+F64, F32_MIXED = 0, 1
+OP_CSR, OP_STENCIL = 0, 1
+M_MAX, P_MAX = 64, 8
+
+
+class CsrC(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("nnz", c_int32), ("rowptr", c_void_p), ("colind", c_void_p), ("values", c_void_p)]
+
+
+class StencilC(ctypes.Structure):
+    _fields_ = [("ndim", c_int32), ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("c_center", c_double),
+                ("c_minus", c_double * 3), ("c_plus", c_double * 3)]
+
+
+class OperatorC(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("csr", CsrC), ("st", StencilC)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("steps", c_int64), ("rejects", c_int64), ("matvecs", c_int64), ("expms", c_int64),
+                ("err_est_sum", c_double), ("krylov_steps", c_int64), ("gs_vectors", c_int64),
+                ("kernel_ms", c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [("gamma", c_double), ("delta", c_double), ("m_init", c_int32), ("m_max", c_int32),
+                ("theta13", c_double), ("breakdown_tol", c_double), ("max_steps", c_int64),
+                ("max_rejects", c_int64), ("precision", c_int32), ("controller", c_int32),
+                ("timeout_cycles", c_int64)]
+
+
+_LIB = None
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/phipm.h."""
+    hdr = open(os.path.join(_build.ROOT, "include", "phipm.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(phipm_[a-z_]+)\s*\(", hdr)))
+
+
+def lib(build_if_needed: bool = True):
+    """Load libphipm.so (building it first when sources are newer)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build_if_needed else _build.LIB
+    L = ctypes.CDLL(path)
+    L.phipm_default_params.argtypes = [ctypes.POINTER(ParamsC)]
+    L.phipm_default_params.restype = None
+    L.phipm_create.argtypes = [ctypes.POINTER(c_void_p), ctypes.POINTER(ParamsC)]
+    L.phipm_create.restype = c_int32
+    L.phipm_destroy.argtypes = [c_void_p]
+    L.phipm_destroy.restype = None
+    L.phipm_last_error.argtypes = [c_void_p]
+    L.phipm_last_error.restype = ctypes.c_char_p
+    L.phipm_set_params.argtypes = [c_void_p, ctypes.POINTER(ParamsC)]
+    L.phipm_set_params.restype = c_int32
+    L.phipm_solve.argtypes = [c_void_p, c_double, ctypes.POINTER(OperatorC), c_int32, ctypes.POINTER(c_void_p),
+                              c_double, c_int32, c_void_p, ctypes.POINTER(StatsC), c_void_p]
+    L.phipm_solve.restype = c_int32
+    L.phipm_solve_host.argtypes = L.phipm_solve.argtypes
+    L.phipm_solve_host.restype = c_int32
+    L.phipm_solve_batched.argtypes = [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(OperatorC),
+                                      ctypes.POINTER(c_int32), ctypes.POINTER(ctypes.POINTER(c_void_p)),
+                                      ctypes.POINTER(c_double), ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p),
+                                      ctypes.POINTER(StatsC), ctypes.POINTER(c_int32), c_void_p]
+    L.phipm_solve_batched.restype = c_int32
+    _LIB = L
+    return L
+
+
+class PhipmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"phipm status {status}: {msg}")
+        self.status = status
+
+
+def default_params() -> ParamsC:
+    p = ParamsC()
+    lib().phipm_default_params(ctypes.byref(p))
+    return p
+
+
+# --------------------------------------------------------------------------------------
+# operators
+# --------------------------------------------------------------------------------------
+class DeviceOperator:
+    """A on the device: CSR arrays as torch tensors (int32 / int32 / float64) or stencil coefficients."""
+
+    def __init__(self, op, device="cuda"):
+        import torch
+        self.src = op
+        self.c = OperatorC()
+        if hasattr(op, "rowptr"):
+            self.rowptr = torch.as_tensor(np.asarray(op.rowptr, dtype=np.int32)).to(device)
+            self.colind = torch.as_tensor(np.asarray(op.colind, dtype=np.int32)).to(device)
+            self.values = torch.as_tensor(np.asarray(op.values, dtype=np.float64)).to(device)
+            self.c.kind = OP_CSR
+            self.c.csr = CsrC(int(op.n), int(self.values.numel()), self.rowptr.data_ptr(), self.colind.data_ptr(),
+                              self.values.data_ptr())
+            self.n = int(op.n)
+        else:
+            self.c.kind = OP_STENCIL
+            self.c.st = stencil_c(op)
+            self.n = int(op.n)
+
+
+def stencil_c(st) -> StencilC:
+    c = StencilC()
+    c.ndim, c.nx, c.ny, c.nz = int(st.ndim), int(st.nx), int(st.ny), int(st.nz)
+    c.c_center = float(st.c_center)
+    for d in range(3):
+        c.c_minus[d] = float(st.c_minus[d])
+        c.c_plus[d] = float(st.c_plus[d])
+    return c
+
+
+class HostOperator:
+    """A in host memory (for phipm_solve_host)."""
+
+    def __init__(self, op):
+        self.c = OperatorC()
+        if hasattr(op, "rowptr"):
+            self.rowptr = np.ascontiguousarray(op.rowptr, dtype=np.int32)
+            self.colind = np.ascontiguousarray(op.colind, dtype=np.int32)
+            self.values = np.ascontiguousarray(op.values, dtype=np.float64)
+            self.c.kind = OP_CSR
+            self.c.csr = CsrC(int(op.n), int(self.values.size), self.rowptr.ctypes.data, self.colind.ctypes.data,
+                              self.values.ctypes.data)
+        else:
+            self.c.kind = OP_STENCIL
+            self.c.st = stencil_c(op)
+        self.n = int(op.n)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------------------
+# solver handle
+# --------------------------------------------------------------------------------------
+class Phipm:
+    """A library handle: owns the device workspace.
+
+    precision: "f64" (PHIPM_F64) or "f32" (PHIPM_F32_MIXED); other keyword
+    arguments override phipm_params fields (gamma, delta, m_init, m_max, ...)."""
+
+    def __init__(self, precision: str = "f64", **overrides):
+        L = lib()
+        self.params = default_params()
+        self.params.precision = F32_MIXED if precision == "f32" else F64
+        for k, v in overrides.items():
+            setattr(self.params, k, v)
+        h = c_void_p()
+        st = L.phipm_create(ctypes.byref(h), ctypes.byref(self.params))
+        if st != OK:
+            raise PhipmError(st, "phipm_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phipm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().phipm_last_error(self.h).decode()
+
+    def _check(self, st):
+        if st != OK:
+            raise PhipmError(st, self.last_error())
+
+    def solve(self, t_end: float, A: DeviceOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,
+              stream=None, check: bool = True):
+        """u(t_end) for device tensors b[k] (float64, length n).  Returns (u, stats dict, status)."""
+        import torch
+        n = A.n
+        p = len(b) - 1
+        for x in b:
+            if x.dtype != torch.float64 or not x.is_cuda or x.numel() != n or not x.is_contiguous():
+                raise ValueError("b[k] must be contiguous float64 CUDA tensors of length n")
+        u = out if out is not None else torch.empty(n, dtype=torch.float64, device=b[0].device)
+        bp = (c_void_p * (p + 1))(*[x.data_ptr() for x in b])
+        stats = StatsC()
+        st = lib().phipm_solve(self.h, float(t_end), ctypes.byref(A.c), p, bp, float(tol), int(symm),
+                               c_void_p(u.data_ptr()), ctypes.byref(stats), _stream_ptr(stream))
+        if check:
+            self._check(st)
+        return u, stats.as_dict(), st
+
+    def solve_host(self, t_end: float, A: HostOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,
+                   stream=None, check: bool = True):
+        """Same with host arrays (numpy float64, or pinned CPU torch tensors)."""
+        p = len(b) - 1
+        ptrs = [(x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data) for x in b]
+        if out is None:
+            out = np.empty(A.n, dtype=np.float64)
+        uptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        bp = (c_void_p * (p + 1))(*ptrs)
+        stats = StatsC()
+        st = lib().phipm_solve_host(self.h, float(t_end), ctypes.byref(A.c), p, bp, float(tol), int(symm),
+                                    c_void_p(uptr), ctypes.byref(stats), _stream_ptr(stream))
+        if check:
+            self._check(st)
+        return out, stats.as_dict(), st
+
+    def solve_batched(self, t_end: list, ops: list, bs: list, tol: list, symm: list, outs: list = None,
+                      stream=None, check: bool = True):
+        """count independent problems in one persistent launch.  Returns (us, stats list, statuses)."""
+        import torch
+        cnt = len(ops)
+        if outs is None:
+            outs = [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in ops]
+        T = (c_double * cnt)(*[float(x) for x in t_end])
+        Aa = (OperatorC * cnt)(*[A.c for A in ops])
+        P = (c_int32 * cnt)(*[len(b) - 1 for b in bs])
+        rows = [(c_void_p * len(b))(*[x.data_ptr() for x in b]) for b in bs]
+        B = (ctypes.POINTER(c_void_p) * cnt)(*[ctypes.cast(r, ctypes.POINTER(c_void_p)) for r in rows])
+        TOL = (c_double * cnt)(*[float(x) for x in tol])
+        SY = (c_int32 * cnt)(*[int(x) for x in symm])
+        U = (c_void_p * cnt)(*[u.data_ptr() for u in outs])
+        ST = (StatsC * cnt)()
+        PS = (c_int32 * cnt)()
+        st = lib().phipm_solve_batched(self.h, cnt, T, Aa, P, B, TOL, SY, U, ST, PS, _stream_ptr(stream))
+        if check:
+            self._check(st)
+        return outs, [s.as_dict() for s in ST], list(PS)

@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle and with
+exact truths.  Bar: relative 2-norm error <= 1e-8 in FP64 mode and <= 1e-5 in
+the FP32 basis mode, the tolerances the method is specified to meet."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import phipm_oracle as O
+from oracle import truth as T
+from paper_0907_4631_gb300 import phipm as pm
+from paper_0907_4631_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-8
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def solver64():
+    return pm.Phipm("f64")
+
+
+@pytest.fixture(scope="module")
+def solver32():
+    return pm.Phipm("f32")
+
+
+def _dev(b):
+    return [torch.as_tensor(np.ascontiguousarray(x)).cuda() for x in b]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _gpu(solver, pr, symm=None):
+    A = pm.DeviceOperator(pr.op)
+    u, st, _ = solver.solve(pr.t_end, A, _dev(pr.b), pr.tol, pr.symm if symm is None else symm)
+    torch.cuda.synchronize()
+    return u.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("as_csr", [False, True])
+def test_c1_laplacian_32(solver64, as_csr):
+    """Plain FP64 configuration: 32x32 Laplacian, p=3, t=0.01, tol 1e-8 (Lanczos)."""
+    pr = wl.laplacian_2d_problem(as_csr=as_csr)
+    u, st = _gpu(solver64, pr, symm=-1)
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, -1)
+    assert _rel(u, ref) <= TOL64
+    assert _rel(u, T.solution_laplacian(2, 32, pr.b, pr.t_end)) <= TOL64
+    assert st["steps"] == rst.steps and st["rejects"] == rst.rejects
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 4])
+def test_small_convdiff_cta_path(solver64, p):
+    pr = wl.convdiff_2d_problem(N=40, p=p, t_end=1e-3, tol=1e-8, seed=2040 + p)
+    u, st = _gpu(solver64, pr)
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    assert _rel(u, ref) <= TOL64
+    assert st["steps"] == rst.steps
+
+
+@pytest.mark.parametrize("N,p", [(130, 4), (171, 2)])
+def test_convdiff_grid_path(solver64, N, p):
+    """n = N^2 >= 16384 runs on every SM; N = 171 gives a ragged tail (n not a multiple of 64)."""
+    pr = wl.convdiff_2d_problem(N=N, p=p, t_end=1e-3, tol=1e-8, seed=2100 + N)
+    u, st = _gpu(solver64, pr)
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    assert _rel(u, ref) <= TOL64
+    assert st["steps"] == rst.steps
+
+
+def test_laplacian_grid_lanczos(solver64):
+    pr = wl.laplacian_2d_problem(N=150, p=2, t_end=2e-3, tol=1e-8, seed=1150)
+    u, st = _gpu(solver64, pr, symm=-1)
+    assert _rel(u, T.solution_laplacian(2, 150, pr.b, pr.t_end)) <= TOL64
+
+
+def test_c2_full_size(solver64):
+    """FP64 nonsymmetric configuration at full size: 512^2 convection-diffusion, CSR, p=4."""
+    pr = wl.convdiff_2d_problem()
+    u, st = _gpu(solver64, pr)
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    assert _rel(u, ref) <= TOL64
+    assert st["steps"] >= 1
+
+
+@pytest.mark.parametrize("N", [24, 40])
+def test_f32_laplacian_3d(solver32, N):
+    pr = wl.laplacian_3d_problem(N=N, p=2, t_end=1e-4, tol=1e-5, seed=3000 + N)
+    u, st = _gpu(solver32, pr)
+    ref, _ = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 1)
+    assert _rel(u, ref) <= TOL32
+    assert _rel(u, T.solution_laplacian(3, N, pr.b, pr.t_end)) <= TOL32
+
+
+def test_c3_full_size_f32(solver32):
+    """Precision form at full size: 128^3 Laplacian stencil, FP32 basis, p=2, tol 1e-5,
+    checked against the sine eigen-expansion (exact)."""
+    pr = wl.laplacian_3d_problem()
+    u, st = _gpu(solver32, pr)
+    assert _rel(u, T.solution_laplacian(3, 128, pr.b, pr.t_end)) <= TOL32
+
+
+def test_f32_convdiff_csr(solver32):
+    pr = wl.convdiff_2d_problem(N=64, p=3, t_end=1e-3, tol=1e-5, seed=2064)
+    u, st = _gpu(solver32, pr)
+    ref, _ = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    assert _rel(u, ref) <= TOL32
+
+
+def test_edge_cases(solver64):
+    A = wl.laplacian(2, 6)
+    n = A.n
+    z = np.zeros(n)
+    u, st = _gpu(solver64, wl.Problem("zero", A, [z, z, z], 1e-2, 1e-8, 1))
+    assert np.all(u == 0) and st["steps"] == 0
+    b1 = wl.normal(4, 1, n)
+    u, _ = _gpu(solver64, wl.Problem("b0zero", A, [z, b1], 1e-2, 1e-10, 1))
+    ref, _ = O.phipm(1e-2, A, [z, b1], 1e-10, 1)
+    assert _rel(u, ref) <= TOL64
+    Z = wl.dense_to_csr(np.zeros((5, 5)))
+    Z = wl.CSR(5, np.zeros(6, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    bz = [wl.normal(4, k, 5) for k in range(4)]
+    u, _ = _gpu(solver64, wl.Problem("Azero", Z, bz, 0.3, 1e-8, -1))
+    assert np.allclose(u, sum(0.3 ** k / np.prod(range(1, k + 1)) * bk for k, bk in enumerate(bz)), rtol=1e-14)
+    small = wl.random_sparse(3, 5, 3, 1.0)                    # n < m: happy breakdown
+    bs = [wl.normal(5, k, 5) for k in range(3)]
+    u, _ = _gpu(solver64, wl.Problem("tiny", small, bs, 1.0, 1e-12, -1))
+    assert np.allclose(u, T.solution_dense_augmented(wl.csr_to_dense(small), bs, 1.0), rtol=1e-11, atol=1e-12)
+    one = wl.dense_to_csr(np.array([[-3.0]]))                  # n = 1
+    u, _ = _gpu(solver64, wl.Problem("one", one, [np.array([2.0]), np.array([1.0])], 0.5, 1e-12, -1))
+    assert u[0] == pytest.approx(np.exp(-1.5) * 2.0 + 0.5 * T.phi_scalar(1, -1.5) * 1.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("p", [0, 3])
+def test_dense_truth_nonsymmetric(solver64, p):
+    A = wl.random_sparse(11, 60, 5, 3.0)
+    b = [wl.normal(11, 10 + k, 60) for k in range(p + 1)]
+    u, _ = _gpu(solver64, wl.Problem("rs", A, b, 2.0, 1e-10, -1))
+    assert np.linalg.norm(u - T.solution_dense_augmented(wl.csr_to_dense(A), b, 2.0)) <= 5e-10
+
+
+def test_invalid_arguments(solver64):
+    pr = wl.laplacian_2d_problem(N=8, p=1)
+    A = pm.DeviceOperator(pr.op)
+    b = _dev(pr.b)
+    for kwargs, bad in [(dict(symm=2), "symm"), (dict(tol=float("nan")), "tol")]:
+        _, _, st = solver64.solve(pr.t_end, A, b, check=False, **{"tol": 1e-8, "symm": 1, **kwargs})
+        assert st == pm.EINVAL, bad
+    _, _, st = solver64.solve(-1.0, A, b, 1e-8, 1, check=False)
+    assert st == pm.EINVAL
+    _, _, st = solver64.solve(pr.t_end, A, b * 5, 1e-8, 1, check=False)     # p = 9 > 8
+    assert st == pm.EINVAL
+
+
+def test_host_api_matches_device_api(solver64):
+    pr = wl.convdiff_2d_problem(N=48, p=2, t_end=1e-3, tol=1e-8, seed=2048)
+    u_dev, st_dev = _gpu(solver64, pr)
+    u_host, st_host, _ = solver64.solve_host(pr.t_end, pm.HostOperator(pr.op), pr.b, pr.tol, 0)
+    assert np.array_equal(u_dev, u_host) and st_dev == st_host
+
+
+def test_deterministic(solver64):
+    pr = wl.convdiff_2d_problem(N=140, p=3, t_end=1e-3, tol=1e-8, seed=2140)
+    u1, _ = _gpu(solver64, pr)
+    u2, _ = _gpu(solver64, pr)
+    assert np.array_equal(u1, u2)
+
+
+def test_batched_small(solver64):
+    probs = wl.batched_convdiff_problems(count=6, side_lo=16, side_hi=48, seed0=4900)
+    ops = [pm.DeviceOperator(p_.op) for p_ in probs]
+    us, stats, sts = solver64.solve_batched([p_.t_end for p_ in probs], ops, [_dev(p_.b) for p_ in probs],
+                                            [p_.tol for p_ in probs], [0] * len(probs))
+    torch.cuda.synchronize()
+    for p_, u, st in zip(probs, us, stats):
+        ref, rst = O.phipm(p_.t_end, p_.op, p_.b, p_.tol, 0)
+        assert _rel(u.cpu().numpy(), ref) <= TOL64
+        assert st["steps"] == rst.steps
