@@ -378,7 +378,7 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
 
   if (n >= kGridMinN) {
     const long long ld = round_ld(n);
-    const size_t vbytes = (size_t)M1 * ld * es, wbytes = (size_t)std::max(p, 1) * ld * 8, ybytes = 2 * (size_t)ld * es;
+    const size_t vbytes = (size_t)M1 * ld * es, wbytes = (size_t)(p + 1) * ld * 8, ybytes = 2 * (size_t)ld * es;
     if (!h->ws.ensure(vbytes + wbytes + ybytes)) return fail(h, PHIPM_ENOMEM, "workspace");
     P.V = h->ws.p;
     P.W = (double*)((char*)h->ws.p + vbytes);
@@ -405,10 +405,10 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
     lay.ld = round_ld(n);
     lay.v_off = 0;
     lay.w_off = (long long)M1 * lay.ld * es;
-    lay.y_off = lay.w_off + (long long)std::max(p, 1) * lay.ld * 8;
+    lay.y_off = lay.w_off + (long long)(p + 1) * lay.ld * 8;
     lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
     lay.e_off = (lay.e_off + 255) & ~255ll;
-    lay.bytes = lay.e_off + 9ll * PM_NA2 * 8;
+    lay.bytes = (lay.e_off + 9ll * PM_NA2 * 8 + 255) & ~255ll;   // slots stay 256-byte aligned
     if (!h->ws.ensure((size_t)lay.bytes)) return fail(h, PHIPM_ENOMEM, "workspace");
     if (!h->probs.ensure(sizeof(DevProblem)) || !h->order.ensure(sizeof(int)) ||
         !h->probs_host.ensure(sizeof(DevProblem) + sizeof(int)))
@@ -551,10 +551,10 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   lay.ld = round_ld(nmax);
   lay.v_off = 0;
   lay.w_off = (long long)M1 * lay.ld * es;
-  lay.y_off = lay.w_off + (long long)pmax * lay.ld * 8;
+  lay.y_off = lay.w_off + (long long)(pmax + 1) * lay.ld * 8;
   lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
   lay.e_off = (lay.e_off + 255) & ~255ll;
-  lay.bytes = lay.e_off + 9ll * PM_NA2 * 8;
+  lay.bytes = (lay.e_off + 9ll * PM_NA2 * 8 + 255) & ~255ll;   // slots stay 256-byte aligned
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f32 ? (const void*)k_solve_queue<float> : (const void*)k_solve_queue<double>,
                                                 PM_THREADS, sizeof(PmShared));

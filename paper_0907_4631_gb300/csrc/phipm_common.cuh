@@ -51,7 +51,7 @@ struct DevProblem {
   double* u;             // current solution u(t_k) = w_0, FP64, caller's buffer
   // workspace (device)
   void* V;               // (m_max+1) basis vectors of length ld, element type S
-  double* W;             // w_1..w_p, FP64, length ld each
+  double* W;             // w_1..w_p and one spare vector, FP64, length ld each
   void* Y;               // 2 buffers of length ld (unnormalised Krylov vector), type S
   long long ld;
 };

@@ -12,6 +12,9 @@
 #pragma once
 #include "phipm_common.cuh"
 
+// FP32 basis mode: bound on ||F|| / ||u|| per step (F = tau^p phi_p(tau A) w_p)
+#define PM_F32_AMP 32.0
+
 template <class S> struct Elem;
 template <> struct Elem<double> {
   typedef double Acc;
@@ -40,6 +43,7 @@ struct PmShared {
   double phi0[PM_NA], phi1[PM_NA];     // phi_p(tau H) e1 and phi_{p+1}(tau H) e1
   double ucoef[PM_NSLOT + PM_MAXP + 1];
   double mat_norm;
+  double dred[PM_NSLOT + PM_WARPS];    // per-unit partial dots (vector, row chunk)
   int ipiv[PM_NA];
   int flag;
 };
@@ -161,6 +165,127 @@ struct LoadDtoF {                         // FP64 vector scaled, rounded to floa
   const double* p; double s;
   __device__ __forceinline__ float operator()(int i) const { return (float)(p[i] * s); }
 };
+
+// ------------------------------------------------------------------------------------
+// Gram-Schmidt passes over this CTA's rows [lo, hi)
+// ------------------------------------------------------------------------------------
+// d_i = sum_r V[i0+i][r] y[r], i < nv, into s.coef[0..nv).  Work is split into
+// units (vector i, row chunk c) handled by one warp each, so the cross-lane sum
+// runs once per unit rather than once per vector per warp.
+template <class S> struct Quad;
+template <> struct Quad<float> {
+  float x[4];
+  __device__ __forceinline__ void load(const float* p) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+  }
+  __device__ __forceinline__ void store(float* p) const { *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <> struct Quad<double> {
+  double x[4];
+  __device__ __forceinline__ void load(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  }
+  __device__ __forceinline__ void store(double* p) const {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+  }
+};
+
+// d_i = sum_r V[i0+i][r] y[r], i < nv, into s.coef[0..nv).  Work is split into
+// units (vector i, row chunk c) handled by one warp each, so the cross-lane sum
+// runs once per unit rather than once per vector per warp.  lo is a multiple of
+// 64 and vectors are 256-byte aligned, so chunks start on 16-byte boundaries.
+template <class S>
+__device__ void dots_cta(const S* __restrict__ V, long long ld, int i0, int nv, const S* __restrict__ y, int lo, int hi,
+                         PmShared& s) {
+  typedef Elem<S> E;
+  typedef typename E::Acc Acc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = hi - lo;
+  int cpv = (PM_WARPS + nv - 1) / nv;                     // chunks per vector
+  cpv = max(1, min(cpv, (rows + 255) / 256));
+  const int units = nv * cpv;
+  const int chunk = (((rows + cpv - 1) / cpv) + 127) & ~127;
+  for (int un = warp; un < units; un += PM_WARPS) {
+    const int i = un / cpv, c = un - i * cpv;
+    const int a = lo + c * chunk;
+    const int b = min(hi, a + chunk);
+    const S* v = V + (size_t)(i0 + i) * ld;
+    Acc acc0 = E::zero(), acc1 = E::zero();
+    int e = a + 4 * lane;
+    for (; e + 128 + 3 < b; e += 256) {
+      Quad<S> v0, y0, v1, y1;
+      v0.load(v + e); y0.load(y + e); v1.load(v + e + 128); y1.load(y + e + 128);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { E::dot(acc0, v0.x[k], y0.x[k]); E::dot(acc1, v1.x[k], y1.x[k]); }
+    }
+    for (; e + 3 < b; e += 128) {
+      Quad<S> v0, y0;
+      v0.load(v + e); y0.load(y + e);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) E::dot(acc0, v0.x[k], y0.x[k]);
+    }
+    for (int r = e; r < b && r < e + 4; ++r) E::dot(acc1, v[r], y[r]);
+    const double d = pm_warp_sum(E::val(acc0) + E::val(acc1));
+    if (lane == 0) s.dred[un] = d;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < cpv; ++c) t += s.dred[i * cpv + c];
+    s.coef[i] = t;
+  }
+  __syncthreads();
+}
+
+// y[r] -= sum_{i<nv} h_i V[i][r] over this CTA's rows, four consecutive rows per
+// thread; returns this thread's sum of y[r]^2.  Element types: FP64 with FP64
+// coefficients, or FP32 with the coefficients rounded to FP32 (FP32 accumulation).
+template <class S, class C>
+__device__ __forceinline__ double update_rows(S* __restrict__ y, const S* __restrict__ V, long long ld, int nv,
+                                              const C* h, int lo, int hi) {
+  double nrm = 0.0;
+  for (int r = lo + 4 * threadIdx.x; r < hi; r += 4 * blockDim.x) {
+    if (r + 3 < hi) {
+      Quad<S> a, b;
+      a.load(y + r);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) b.x[k] = S(0);
+      int i = 0;
+      for (; i + 1 < nv; i += 2) {
+        Quad<S> v0, v1;
+        v0.load(V + (size_t)i * ld + r);
+        v1.load(V + (size_t)(i + 1) * ld + r);
+        const S h0 = (S)h[i], h1 = (S)h[i + 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { a.x[k] = fma(-h0, v0.x[k], a.x[k]); b.x[k] = fma(-h1, v1.x[k], b.x[k]); }
+      }
+      if (i < nv) {
+        Quad<S> v0;
+        v0.load(V + (size_t)i * ld + r);
+        const S h0 = (S)h[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.x[k] = fma(-h0, v0.x[k], a.x[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        a.x[k] += b.x[k];
+        nrm = fma((double)a.x[k], (double)a.x[k], nrm);
+      }
+      a.store(y + r);
+    } else {
+      for (int q = r; q < hi; ++q) {
+        S a = y[q];
+        for (int i = 0; i < nv; ++i) a = fma(-(S)h[i], V[(size_t)i * ld + q], a);
+        y[q] = a;
+        nrm = fma((double)a, (double)a, nrm);
+      }
+    }
+  }
+  return nrm;
+}
 
 // ------------------------------------------------------------------------------------
 // dense kernels of one CTA on small matrices (FP64): the exponential of H_hat
@@ -330,7 +455,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   S* V = (S*)P.V;
   S* Y = (S*)P.Y;
   double* W = P.W;
-  double* u = P.u;
+  double* u = P.u;                        // current solution u(t_k)
+  double* ualt = P.W + (size_t)p * P.ld;  // spare vector (FP32 guard)
   int parity = 0;
   int status = PM_OK;
   long long steps = 0, rejects = 0, matvecs = 0, expms = 0, kry_steps = 0, gs_vectors = 0;
@@ -428,7 +554,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     int nonfinite = 0;
     while (t < t_end) {
       // ---------------- w-recurrence (a2), Eq. (wrecurrence): p SpMVs in FP64
-      double beta;
+      double beta, unorm;
       {
         double tl[PM_MAXP + 1];
         tl[0] = 1.0;
@@ -446,9 +572,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           }
           matvecs += 1;
           if (j == p) {
-            double v[8] = {nrm, 0, 0, 0, 0, 0, 0, 0};
-            block_sum8(s, v, 1, s.coef);
-            PM_SUM_OR_FAIL(1);
+            double un = 0.0;
+            for (int r = lo + tid; r < hi; r += nth) un = fma(u[r], u[r], un);
+            double v[8] = {nrm, un, 0, 0, 0, 0, 0, 0};
+            block_sum8(s, v, 2, s.coef);
+            PM_SUM_OR_FAIL(2);
           } else {
             PM_SYNC_OR_FAIL();
           }
@@ -456,11 +584,12 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         if (p == 0) {
           double nrm = 0.0;
           for (int r = lo + tid; r < hi; r += nth) nrm = fma(u[r], u[r], nrm);
-          double v[8] = {nrm, 0, 0, 0, 0, 0, 0, 0};
-          block_sum8(s, v, 1, s.coef);
-          PM_SUM_OR_FAIL(1);
+          double v[8] = {nrm, nrm, 0, 0, 0, 0, 0, 0};
+          block_sum8(s, v, 2, s.coef);
+          PM_SUM_OR_FAIL(2);
         }
         beta = sqrt(s.coef[0]);
+        unorm = sqrt(s.coef[1]);
       }
       const double* wp = (p == 0) ? u : W + (size_t)(p - 1) * ld;
       int kcur = 0;            // Arnoldi / Lanczos steps done for this w_p
@@ -529,23 +658,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               if (!lanczos) gs_vectors += j + 1;
               const int i0 = lanczos ? j : 0;          // Lanczos: only t_jj = v_j^T y here
               const int nv = j + 1 - i0;
-              // dots d_i = v_i . y over my rows, groups of 8
-              for (int g = 0; g < nv; g += 8) {
-                const int cnt = min(8, nv - g);
-                Acc acc[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = E::zero();
-                for (int r = lo + tid; r < hi; r += nth) {
-                  const S yv = ycur[r];
-#pragma unroll
-                  for (int k = 0; k < 8; ++k)
-                    if (k < cnt) E::dot(acc[k], V[(size_t)(i0 + g + k) * ld + r], yv);
-                }
-                double v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = E::val(acc[k]);
-                block_sum8(s, v, cnt, s.coef + g);
-              }
+              // dots d_i = v_i . y over my rows
+              dots_cta<S>(V, ld, i0, nv, ycur, lo, hi, s);
               PM_SUM_OR_FAIL(nv);
               if (lanczos) {
                 // Algorithm 2: y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
@@ -577,38 +691,12 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
                 for (int k = tid; k < nv; k += nth) { s.h1[k] = s.coef[k]; s.hf[k] = E::coef(s.coef[k]); }
                 __syncthreads();
                 for (int pass = 0; pass < 2; ++pass) {
-                  double nrm = 0.0;
-                  for (int r = lo + tid; r < hi; r += nth) {
-                    if (sizeof(S) == 8) {
-                      double y = (double)ycur[r];
-                      for (int i = 0; i < nv; ++i) y = fma(-s.h1[i], (double)V[(size_t)i * ld + r], y);
-                      ycur[r] = (S)y;
-                      nrm = fma(y, y, nrm);
-                    } else {
-                      float y = (float)ycur[r];
-                      for (int i = 0; i < nv; ++i) y = fmaf(-s.hf[i], (float)V[(size_t)i * ld + r], y);
-                      ycur[r] = (S)y;
-                      nrm = fma((double)y, (double)y, nrm);
-                    }
-                  }
+                  double nrm;
+                  if (sizeof(S) == 8) nrm = update_rows<S, double>(ycur, V, ld, nv, s.h1, lo, hi);
+                  else nrm = update_rows<S, float>(ycur, V, ld, nv, s.hf, lo, hi);
                   __syncthreads();
                   if (pass == 0) {
-                    for (int g = 0; g < nv; g += 8) {
-                      const int cnt = min(8, nv - g);
-                      Acc acc[8];
-#pragma unroll
-                      for (int k = 0; k < 8; ++k) acc[k] = E::zero();
-                      for (int r = lo + tid; r < hi; r += nth) {
-                        const S yv = ycur[r];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                          if (k < cnt) E::dot(acc[k], V[(size_t)(g + k) * ld + r], yv);
-                      }
-                      double v[8];
-#pragma unroll
-                      for (int k = 0; k < 8; ++k) v[k] = E::val(acc[k]);
-                      block_sum8(s, v, cnt, s.coef + g);
-                    }
+                    dots_cta<S>(V, ld, 0, nv, ycur, lo, hi, s);
                     PM_SUM_OR_FAIL(nv);
                     for (int k = tid; k < nv; k += nth) {
                       const double h2 = s.coef[k];
@@ -748,7 +836,6 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         }
         if (omega <= prm.delta) {
           // ---------------- accept: Eq. (step) (a8), F by Eq. (phipapprox2)
-          accepted = true;
           if (tid == 0) {
             const double tp = pow(tau_used, p);
             if (beta > 0.0) {
@@ -762,14 +849,39 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             }
           }
           __syncthreads();
+          // FP32 basis: F carries a relative rounding error of about u32 and cancels against
+          // sum_j tau^j/j! w_j in Eq. (step); the candidate goes to a spare vector so that
+          // ||F|| / ||u_new|| can be bounded before it replaces u.
+          const bool guard = (sizeof(S) == 4) && p >= 2 && beta > 0.0;
+          double* udst = guard ? ualt : u;
           const int nvv = (beta > 0.0) ? ((s.ucoef[m_used] != 0.0) ? m_used + 1 : m_used) : 0;
+          double un = 0.0;
           for (int r = lo + tid; r < hi; r += nth) {
             double acc = 0.0;
             for (int i = 0; i < nvv; ++i) acc = fma(s.ucoef[i], (double)V[(size_t)i * ld + r], acc);
             if (p >= 1) acc = fma(s.ucoef[PM_NSLOT], u[r], acc);
             for (int jj = 1; jj < p; ++jj) acc = fma(s.ucoef[PM_NSLOT + jj], W[(size_t)(jj - 1) * ld + r], acc);
-            u[r] = acc;
+            udst[r] = acc;
+            un = fma(acc, acc, un);
           }
+          if (guard) {
+            double v[8] = {un, 0, 0, 0, 0, 0, 0, 0};
+            block_sum8(s, v, 1, s.coef);
+            PM_SUM_OR_FAIL(1);
+            const double unew = sqrt(s.coef[0]);
+            double fn = 0.0;
+            for (int i = 0; i < m_used; ++i) fn = fma(s.phi0[i], s.phi0[i], fn);
+            fn = pow(tau_used, p) * beta * sqrt(fn);
+            if (fn > PM_F32_AMP * unew && unew > 0.0) {
+              rejects += 1;
+              if (rejects > prm.max_rejects) { status = PM_EMAXSTEPS; goto done; }
+              tau = tau_used * pow(0.5 * PM_F32_AMP * unew / fn, 1.0 / (double)(p - 1));
+              ctl.rejected = ctl.tau_changed = ctl.m_changed = ctl.qf = ctl.kf = false;
+              continue;
+            }
+            double* t2 = u; u = ualt; ualt = t2;
+          }
+          accepted = true;
           steps += 1;
           err_sum += eps;
           if (steps > prm.max_steps) { status = PM_EMAXSTEPS; goto done; }
@@ -791,6 +903,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         }
       }
     }
+  }
+  if (u != P.u) {
+    for (int r = lo + tid; r < hi; r += nth) P.u[r] = u[r];
   }
 done:
   if (team.rank() == 0 && threadIdx.x == 0) {
