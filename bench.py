@@ -35,10 +35,12 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "convdiff2d_512": dict(metric_cfg="FP64 nonsymmetric (Arnoldi) convection-diffusion 512x512 CSR, p=4",
-                           precision="f64"),
-    "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64"),
+                           precision="f64pair"),
+    "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64pair"),
     "laplacian3d_128": dict(metric_cfg="FP32-basis 128^3 Laplacian stencil, p=2, tol 1e-5", precision="f32"),
 }
+DTYPES = {"f64": "f64", "f32": "f32 basis (FP64 coefficients, H, expm, eps, u)",
+          "f64pair": "f32x2 float pairs on the FP32 pipe (FP64-class; FP64 w-recurrence, H, expm, eps, u)"}
 METRIC = "solves/s at rel.err<=1e-8 vs FP64 oracle; SpMV+Arnoldi HBM GB/s vs peak"
 PEAK_FALLBACK = 6800.0
 
@@ -63,7 +65,7 @@ def measured_peaks():
         return PEAK_FALLBACK, "fallback"
 
 
-def algorithmic_bytes(pr, stats) -> float:
+def algorithmic_bytes(pr, stats, precision) -> float:
     """SpMV + Arnoldi bytes of one solve (per-step model).
 
     CGS2 step j touches j+1 basis vectors four times (two dot passes, two
@@ -71,7 +73,7 @@ def algorithmic_bytes(pr, stats) -> float:
     step also runs one SpMV (CSR: 12 nnz + 4 (n+1) + 2 s n for the x read and
     the y write; stencil: 2 s n) and writes the new basis vector (s n)."""
     n = pr.n
-    s = 4 if pr.precision == "f32" else 8
+    s = 4 if precision == "f32" else 8
     if hasattr(pr.op, "rowptr"):
         spmv = 12 * pr.op.nnz + 4 * (n + 1) + 2 * s * n
     else:
@@ -302,7 +304,7 @@ def main():
 
     peak, peak_kind = measured_peaks()
     kernel_ms = statistics.mean(kms)
-    abytes = algorithmic_bytes(pr, stats)
+    abytes = algorithmic_bytes(pr, stats, spec["precision"])
     achieved = abytes / (kernel_ms / 1e3) / 1e9
     kernel_name = "k_solve_grid" if pr.n >= 16384 else "k_solve_queue"
     traffic = traffic_from_profiles(kernel_name, args.workload)
@@ -313,7 +315,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if spec["precision"] == "f32" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[spec["precision"]],
         "data": "synthetic (seeded counter-based generator; same inputs as the oracle)",
         "config": {"workload": args.workload, "n": pr.n, "nnz": int(pr.op.nnz if hasattr(pr.op, "rowptr") else pr.op.nnz()),
                    "p": pr.p, "t_end": pr.t_end, "tol": pr.tol, "l2": "flushed between timed solves (256 MiB write)",

@@ -47,9 +47,16 @@ typedef enum {
 } phipm_status;
 
 typedef enum {
-  PHIPM_F64 = 0,          /* basis, SpMV and all vector work in FP64                     */
-  PHIPM_F32_MIXED = 1     /* basis and SpMV in FP32 with FP32 accumulation; Gram-Schmidt
-                             coefficients, norms, H, the exponential, eps and u in FP64   */
+  PHIPM_F64 = 0,          /* basis, SpMV and all vector work in IEEE FP64 (FP64 pipe)        */
+  PHIPM_F32_MIXED = 1,    /* basis and SpMV in FP32 with FP32 accumulation; Gram-Schmidt
+                             dot products accumulated as float pairs; coefficients, norms, H,
+                             the exponential, eps and u in FP64                              */
+  PHIPM_F64_PAIR = 2      /* FP64-class accuracy on the FP32 pipe: the basis is stored as
+                             float pairs hi+lo (8 bytes, about 48 significant bits) and every
+                             SpMV, dot and update of the Krylov phase uses error-free float
+                             transforms; the w-recurrence, H, the exponential, eps and u are
+                             FP64.  Results differ from PHIPM_F64 by about 2^-48 times the
+                             cancellation factor ||F|| / ||u|| of Eq. (step).                 */
 } phipm_precision;
 
 typedef enum { PHIPM_OP_CSR = 0, PHIPM_OP_STENCIL = 1 } phipm_op_kind;

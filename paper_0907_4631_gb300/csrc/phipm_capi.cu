@@ -2,7 +2,8 @@
 // run the device engine (phipm_engine.cuh):
 //   k_solve_grid     one problem, every CTA of a cooperative launch;
 //   k_solve_queue    a persistent CTA per slot that pulls problems from an
-//                    atomic queue (batched form, and single small problems).
+//                    atomic queue, largest first (batched form and small
+//                    single problems).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -22,7 +23,7 @@ k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned* ba
   extern __shared__ __align__(16) unsigned char pm_smem[];
   PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
   GridTeam team{bar, err, prm.timeout_cycles};
-  phipm_device<GridTeam, S>(team, P, prm, *res, s, w, w.expm);
+  phipm_device<GridTeam, S>(team, P, prm, *res, s, w);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int e = *((volatile int*)err);
     if (e != 0 && res->status == PM_OK) res->status = e;
@@ -31,9 +32,9 @@ k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned* ba
 
 // Workspace of one queue slot (one CTA): V, W, Y and the exponential scratch.
 struct SlotLayout {
-  long long ld;          // vector stride (elements)
-  long long v_off, w_off, y_off, e_off;   // byte offsets inside the slot
-  long long bytes;       // bytes per slot
+  long long ld;                          // vector stride (elements)
+  long long v_off, w_off, y_off, e_off;  // byte offsets inside the slot
+  long long bytes;                       // bytes per slot (multiple of 256)
 };
 
 template <class S>
@@ -45,7 +46,7 @@ k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams pr
   __shared__ int s_next;
   unsigned char* base = slots + (size_t)blockIdx.x * lay.bytes;
   CtaTeam team;
-  PmWork w{nullptr, nullptr, (double*)(base + lay.e_off)};
+  PmWork w{nullptr, (double*)(base + lay.e_off)};
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
     __syncthreads();
@@ -58,15 +59,30 @@ k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams pr
     P.W = (double*)(base + lay.w_off);
     P.Y = base + lay.y_off;
     P.ld = lay.ld;
-    phipm_device<CtaTeam, S>(team, P, prm, res[id], s, w, w.expm);
+    phipm_device<CtaTeam, S>(team, P, prm, res[id], s, w);
     __syncthreads();
   }
 }
 
-// FP32 copy of CSR values for the FP32 basis mode
-__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// CSR values converted for the FP32 basis (valf) or the float-pair basis (val2),
+// one CTA per problem.
+__global__ void k_convert_values(const DevProblem* probs, int count, int mode) {
+  const int id = blockIdx.x;
+  if (id >= count) return;
+  const DevOp& A = probs[id].A;
+  if (A.kind != 0) return;
+  const long long nnz = A.nnz;
+  for (long long k = threadIdx.x; k < nnz; k += blockDim.x) {
+    const double v = A.val[k];
+    if (mode == 1) {
+      ((float*)A.valf)[k] = (float)v;
+    } else {
+      df32 d;
+      d.hi = __double2float_rn(v);
+      d.lo = __double2float_rn(v - (double)d.hi);
+      ((df32*)A.val2)[k] = d;
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -110,10 +126,10 @@ struct phipm_handle {
   std::string err;
   DevBuf ws;          // V, W, Y of the grid solve / queue slots
   DevBuf sync;        // barrier words + error flag + queue counter
-  DevBuf partials, phi_g, expm, valf, res, probs, order;
+  DevBuf partials, expm, conv, res, probs, order;
   DevBuf h_rowptr, h_colind, h_vals, h_b, h_u;   // device staging for phipm_solve_host
-  HostBuf res_host, probs_host, order_host;
-  int grid_blocks[2] = {0, 0};   // cooperative grid size per precision
+  HostBuf res_host, probs_host;
+  int grid_blocks[3] = {0, 0, 0};    // cooperative grid size per precision
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the solver kernel
 };
 
@@ -137,7 +153,7 @@ extern "C" void phipm_default_params(phipm_params* o) {
   o->max_rejects = 1000000;
   o->precision = PHIPM_F64;
   o->controller = 0;
-  o->timeout_cycles = 20000000000ll;   // ~10 s at 2 GHz
+  o->timeout_cycles = 20000000000ll;   // about 10 s at 2 GHz
 }
 
 static bool params_ok(const phipm_params& p, std::string& why) {
@@ -146,10 +162,20 @@ static bool params_ok(const phipm_params& p, std::string& why) {
   if (p.m_init < 1 || p.m_init > p.m_max) { why = "m_init out of [1, m_max]"; return false; }
   if (!(p.theta13 > 0)) { why = "theta13 must be positive"; return false; }
   if (!(p.breakdown_tol >= 0)) { why = "breakdown_tol must be >= 0"; return false; }
-  if (p.precision != PHIPM_F64 && p.precision != PHIPM_F32_MIXED) { why = "unknown precision"; return false; }
+  if (p.precision != PHIPM_F64 && p.precision != PHIPM_F32_MIXED && p.precision != PHIPM_F64_PAIR) {
+    why = "unknown precision";
+    return false;
+  }
   if (p.controller != 0 && p.controller != 1) { why = "unknown controller"; return false; }
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
   return true;
+}
+
+template <class S>
+static cudaError_t setup_kernels(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_solve_grid<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_solve_queue<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* params) {
@@ -166,25 +192,23 @@ extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* par
   if (e != cudaSuccess) { delete h; return PHIPM_ECUDA; }
   e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) { delete h; return PHIPM_ECUDA; }
-  int smem = (int)sizeof(PmShared);
-  if (cudaFuncSetAttribute(k_solve_grid<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_solve_grid<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_solve_queue<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_solve_queue<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+  const int smem = (int)sizeof(PmShared);
+  if (setup_kernels<double>(smem) != cudaSuccess || setup_kernels<float>(smem) != cudaSuccess ||
+      setup_kernels<df32>(smem) != cudaSuccess) {
     delete h;
     return PHIPM_ECUDA;
   }
-  int occ0 = 0, occ1 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_solve_grid<double>, PM_THREADS, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_solve_grid<float>, PM_THREADS, smem);
-  h->grid_blocks[0] = std::max(1, occ0) * h->num_sms;
-  h->grid_blocks[1] = std::max(1, occ1) * h->num_sms;
+  int occ[3] = {0, 0, 0};
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve_grid<double>, PM_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve_grid<float>, PM_THREADS, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve_grid<df32>, PM_THREADS, smem);
+  for (int i = 0; i < 3; ++i) h->grid_blocks[i] = std::max(1, occ[i]) * h->num_sms;
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     delete h;
     return PHIPM_ECUDA;
   }
   if (!h->sync.ensure(4096) || !h->res.ensure(sizeof(DevResult)) || !h->res_host.ensure(sizeof(DevResult)) ||
-      !h->phi_g.ensure(2 * 2 * PM_NA * sizeof(double)) || !h->expm.ensure(9 * PM_NA2 * sizeof(double))) {
+      !h->expm.ensure(PM_EXPM_DOUBLES * sizeof(double))) {
     delete h;
     return PHIPM_ENOMEM;
   }
@@ -194,12 +218,11 @@ extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* par
 
 extern "C" void phipm_destroy(phipm_handle* h) {
   if (!h) return;
-  DevBuf* bufs[] = {&h->ws, &h->sync, &h->partials, &h->phi_g, &h->expm, &h->valf, &h->res, &h->probs,
+  DevBuf* bufs[] = {&h->ws, &h->sync, &h->partials, &h->expm, &h->conv, &h->res, &h->probs,
                     &h->order, &h->h_rowptr, &h->h_colind, &h->h_vals, &h->h_b, &h->h_u};
   for (DevBuf* b : bufs) b->release();
   h->res_host.release();
   h->probs_host.release();
-  h->order_host.release();
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -266,7 +289,14 @@ static int op_n(const phipm_operator* A) {
   return A->kind == PHIPM_OP_CSR ? A->csr.n : A->st.nx * A->st.ny * A->st.nz;
 }
 
-static DevOp make_devop(const phipm_operator* A, long long nnz_model, const float* valf) {
+static df32 host_split(double c) {   // c = hi + lo with hi = fl32(c)
+  df32 r;
+  r.hi = (float)c;
+  r.lo = (float)(c - (double)r.hi);
+  return r;
+}
+
+static DevOp make_devop(const phipm_operator* A, long long nnz_model) {
   DevOp o;
   memset(&o, 0, sizeof(o));
   o.kind = A->kind == PHIPM_OP_CSR ? 0 : 1;
@@ -276,20 +306,25 @@ static DevOp make_devop(const phipm_operator* A, long long nnz_model, const floa
     o.rowptr = A->csr.rowptr;
     o.colind = A->csr.colind;
     o.val = A->csr.values;
-    o.valf = valf;
-    o.ndim = 0;
   } else {
     o.ndim = A->st.ndim;
     o.nx = A->st.nx;
     o.ny = A->st.ny;
     o.nz = A->st.nz;
     o.cc = A->st.c_center;
-    for (int d = 0; d < 3; ++d) { o.cm[d] = A->st.c_minus[d]; o.cp[d] = A->st.c_plus[d]; }
+    o.cc2 = host_split(o.cc);
+    for (int d = 0; d < 3; ++d) {
+      o.cm[d] = A->st.c_minus[d];
+      o.cp[d] = A->st.c_plus[d];
+      o.cm2[d] = host_split(o.cm[d]);
+      o.cp2[d] = host_split(o.cp[d]);
+    }
   }
   return o;
 }
 
 static long long round_ld(long long n) { return std::max(64ll, (n + 63) & ~63ll); }
+static size_t elem_bytes(int precision) { return precision == PHIPM_F32_MIXED ? 4 : 8; }
 
 static phipm_status map_status(int s) {
   switch (s) {
@@ -328,8 +363,74 @@ static void fill_stats(phipm_stats* o, const DevResult& r, float kernel_ms) {
   o->kernel_ms = kernel_ms;
 }
 
-// Problems up to this size run on one CTA; larger ones on the whole GPU.
+static SlotLayout slot_layout(long long nmax, int pmax, int m_max, size_t es) {
+  SlotLayout lay;
+  lay.ld = round_ld(nmax);
+  lay.v_off = 0;
+  lay.w_off = (long long)(m_max + 1) * lay.ld * (long long)es;
+  lay.y_off = lay.w_off + (long long)(pmax + 1) * lay.ld * 8;
+  lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
+  lay.e_off = (lay.e_off + 255) & ~255ll;
+  lay.bytes = (lay.e_off + (long long)PM_EXPM_DOUBLES * 8 + 255) & ~255ll;   // slots stay 256-byte aligned
+  return lay;
+}
+
+template <class S>
+static cudaError_t launch_queue(int blocks, cudaStream_t stream, const DevProblem* probs, const int* order, int count,
+                                const DevParams& prm, DevResult* res, unsigned char* slots, const SlotLayout& lay,
+                                int* queue) {
+  k_solve_queue<S><<<blocks, PM_THREADS, sizeof(PmShared), stream>>>(probs, order, count, prm, res, slots, lay, queue);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_queue_any(int precision, int blocks, cudaStream_t stream, const DevProblem* probs,
+                                    const int* order, int count, const DevParams& prm, DevResult* res,
+                                    unsigned char* slots, const SlotLayout& lay, int* queue) {
+  if (precision == PHIPM_F32_MIXED)
+    return launch_queue<float>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+  if (precision == PHIPM_F64_PAIR)
+    return launch_queue<df32>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+  return launch_queue<double>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+}
+
+static int queue_occupancy(int precision) {
+  int occ = 1;
+  const void* f = precision == PHIPM_F32_MIXED ? (const void*)k_solve_queue<float>
+                  : precision == PHIPM_F64_PAIR ? (const void*)k_solve_queue<df32>
+                                                : (const void*)k_solve_queue<double>;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, PM_THREADS, sizeof(PmShared));
+  return std::max(1, occ);
+}
+
+// Problems below this size run on one CTA; larger ones on every SM.
 static const int kGridMinN = 16384;
+
+// Reserve converted-value storage for CSR problems (FP32 / float-pair bases)
+// and point each descriptor at its slice.
+static bool assign_conversions(phipm_handle* h, DevProblem* probs, int count, int precision) {
+  if (precision == PHIPM_F64) return true;
+  const size_t es = precision == PHIPM_F32_MIXED ? 4 : 8;
+  size_t total = 0;
+  for (int i = 0; i < count; ++i)
+    if (probs[i].A.kind == 0) total += ((size_t)probs[i].A.nnz * es + 255) & ~(size_t)255;
+  if (total == 0) return true;
+  if (!h->conv.ensure(total)) return false;
+  size_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    if (probs[i].A.kind != 0) continue;
+    void* p = (char*)h->conv.p + off;
+    if (precision == PHIPM_F32_MIXED) probs[i].A.valf = (const float*)p;
+    else probs[i].A.val2 = (const df32*)p;
+    off += ((size_t)probs[i].A.nnz * es + 255) & ~(size_t)255;
+  }
+  return true;
+}
+
+static bool any_csr(const DevProblem* probs, int count) {
+  for (int i = 0; i < count; ++i)
+    if (probs[i].A.kind == 0 && probs[i].A.nnz > 0) return true;
+  return false;
+}
 
 // ------------------------------------------------------------------------------------
 // single solve
@@ -353,28 +454,24 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
   if (stats) memset(stats, 0, sizeof(*stats));
   if (n == 0) return PHIPM_OK;
 
-  const bool f32 = h->params.precision == PHIPM_F32_MIXED;
-  const size_t es = f32 ? 4 : 8;
-  const float* valf = nullptr;
+  const int prec = h->params.precision;
+  const size_t es = elem_bytes(prec);
   cudaError_t e;
-  if (f32 && A->kind == PHIPM_OP_CSR && A->csr.nnz > 0) {
-    if (!h->valf.ensure((size_t)A->csr.nnz * 4)) return fail(h, PHIPM_ENOMEM, "valf");
-    k_to_float<<<std::min(4 * h->num_sms, (int)((A->csr.nnz + 255) / 256)), 256, 0, stream>>>(
-        A->csr.values, (float*)h->valf.p, A->csr.nnz);
-    valf = (const float*)h->valf.p;
-  }
   DevProblem P;
   memset(&P, 0, sizeof(P));
-  P.A = make_devop(A, nnz_model, valf);
+  P.A = make_devop(A, nnz_model);
   P.p = p;
   P.symm = symm;
   P.t_end = t_end;
   P.tol = tol;
   for (int k = 0; k <= p; ++k) P.b[k] = b[k];
   P.u = u;
+  if (!assign_conversions(h, &P, 1, prec)) return fail(h, PHIPM_ENOMEM, "value conversion buffer");
   const DevParams prm = make_params(h->params);
   const int M1 = h->params.m_max + 1;
   DevResult* res_h = (DevResult*)h->res_host.p;
+  DevResult* res_d = (DevResult*)h->res.p;
+  const bool convert = prec != PHIPM_F64 && any_csr(&P, 1);
 
   if (n >= kGridMinN) {
     const long long ld = round_ld(n);
@@ -384,57 +481,57 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
     P.W = (double*)((char*)h->ws.p + vbytes);
     P.Y = (char*)h->ws.p + vbytes + wbytes;
     P.ld = ld;
-    const int G = h->grid_blocks[f32 ? 1 : 0];
-    if (!h->partials.ensure((size_t)2 * G * PM_NSLOT * sizeof(double))) return fail(h, PHIPM_ENOMEM, "partials");
-    PmWork w{(double*)h->partials.p, (double*)h->phi_g.p, (double*)h->expm.p};
+    const int G = h->grid_blocks[prec];
+    if (!h->partials.ensure((size_t)2 * G * PM_PSTRIDE * sizeof(double))) return fail(h, PHIPM_ENOMEM, "partials");
+    if (convert) {
+      if (!h->probs.ensure(sizeof(DevProblem)) || !h->probs_host.ensure(sizeof(DevProblem)))
+        return fail(h, PHIPM_ENOMEM, "descriptors");
+      memcpy(h->probs_host.p, &P, sizeof(P));
+      if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, sizeof(P), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(h, e, "descriptor upload");
+      k_convert_values<<<1, 1024, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
+    }
+    PmWork w{(double*)h->partials.p, (double*)h->expm.p};
     unsigned* bar = (unsigned*)h->sync.p;
     int* err = (int*)((char*)h->sync.p + 1024);
-    DevResult* res_d = (DevResult*)h->res.p;
     if ((e = cudaMemsetAsync(h->sync.p, 0, 2048, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
     if ((e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
     void* args[] = {(void*)&P, (void*)&prm, (void*)&res_d, (void*)&w, (void*)&bar, (void*)&err};
+    const void* fn = prec == PHIPM_F32_MIXED ? (const void*)k_solve_grid<float>
+                     : prec == PHIPM_F64_PAIR ? (const void*)k_solve_grid<df32>
+                                              : (const void*)k_solve_grid<double>;
     cudaEventRecord(h->ev0, stream);
-    e = cudaLaunchCooperativeKernel(f32 ? (const void*)k_solve_grid<float> : (const void*)k_solve_grid<double>,
-                                    dim3(G), dim3(PM_THREADS), args, sizeof(PmShared), stream);
+    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PM_THREADS), args, sizeof(PmShared), stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch");
     cudaEventRecord(h->ev1, stream);
-    if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-      return cuda_fail(h, e, "result copy");
   } else {
-    SlotLayout lay;
-    lay.ld = round_ld(n);
-    lay.v_off = 0;
-    lay.w_off = (long long)M1 * lay.ld * es;
-    lay.y_off = lay.w_off + (long long)(p + 1) * lay.ld * 8;
-    lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
-    lay.e_off = (lay.e_off + 255) & ~255ll;
-    lay.bytes = (lay.e_off + 9ll * PM_NA2 * 8 + 255) & ~255ll;   // slots stay 256-byte aligned
+    const SlotLayout lay = slot_layout(n, p, h->params.m_max, es);
     if (!h->ws.ensure((size_t)lay.bytes)) return fail(h, PHIPM_ENOMEM, "workspace");
     if (!h->probs.ensure(sizeof(DevProblem)) || !h->order.ensure(sizeof(int)) ||
         !h->probs_host.ensure(sizeof(DevProblem) + sizeof(int)))
       return fail(h, PHIPM_ENOMEM, "descriptors");
     memcpy(h->probs_host.p, &P, sizeof(P));
-    int zero = 0;
+    const int zero = 0;
     memcpy((char*)h->probs_host.p + sizeof(DevProblem), &zero, sizeof(int));
     int* queue = (int*)((char*)h->sync.p + 2048);
-    DevResult* res_d = (DevResult*)h->res.p;
     if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, sizeof(DevProblem), cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + sizeof(DevProblem), sizeof(int), cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(queue, 0, sizeof(int), stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess)
       return cuda_fail(h, e, "descriptor upload");
+    if (convert) {
+      k_convert_values<<<1, 1024, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
+    }
     cudaEventRecord(h->ev0, stream);
-    if (f32)
-      k_solve_queue<float><<<1, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm,
-                                                                        res_d, (unsigned char*)h->ws.p, lay, queue);
-    else
-      k_solve_queue<double><<<1, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm,
-                                                                         res_d, (unsigned char*)h->ws.p, lay, queue);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "launch");
+    e = launch_queue_any(prec, 1, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm, res_d,
+                         (unsigned char*)h->ws.p, lay, queue);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch");
     cudaEventRecord(h->ev1, stream);
-    if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-      return cuda_fail(h, e, "result copy");
   }
+  if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+    return cuda_fail(h, e, "result copy");
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "solve");
   if (stats) {
     float kms = 0.f;
@@ -475,7 +572,7 @@ extern "C" phipm_status phipm_solve_host(phipm_handle* h, double t_end, const ph
     Ad.csr.colind = (const int32_t*)h->h_colind.p;
     Ad.csr.values = (const double*)h->h_vals.p;
   }
-  const size_t vb = (size_t)std::max(n, 1) * 8;
+  const size_t vb = ((size_t)std::max(n, 1) * 8 + 255) & ~(size_t)255;
   if (!h->h_b.ensure(vb * (p + 1)) || !h->h_u.ensure(vb)) return fail(h, PHIPM_ENOMEM, "vector staging");
   const double* bd[PHIPM_P_MAX + 1];
   for (int k = 0; k <= p; ++k) {
@@ -509,12 +606,8 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   if (count < 0) return fail(h, PHIPM_EINVAL, "count < 0");
   if (count == 0) return PHIPM_OK;
   if (!t_end || !A || !p || !b || !tol || !symm || !u) return fail(h, PHIPM_EINVAL, "NULL array argument");
-  const bool f32 = h->params.precision == PHIPM_F32_MIXED;
-  if (f32) {
-    for (int i = 0; i < count; ++i)
-      if (A[i].kind == PHIPM_OP_CSR) return fail(h, PHIPM_EINVAL, "batched FP32 mode takes stencil operators");
-  }
-  const size_t es = f32 ? 4 : 8;
+  const int prec = h->params.precision;
+  const size_t es = elem_bytes(prec);
   std::vector<DevProblem> probs(count);
   std::vector<double> cost(count);
   int nmax = 1, pmax = 1;
@@ -525,11 +618,12 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
     if (!(t_end[i] > 0) || !std::isfinite(t_end[i])) return fail(h, PHIPM_EINVAL, "t_end must be positive and finite");
     if (p[i] < 0 || p[i] > PHIPM_P_MAX) return fail(h, PHIPM_EINVAL, "p out of [0, 8]");
     if (symm[i] < -1 || symm[i] > 1) return fail(h, PHIPM_EINVAL, "symm must be -1, 0 or 1");
+    if (!std::isfinite(tol[i])) return fail(h, PHIPM_EINVAL, "tol must be finite");
     const int n = op_n(&A[i]);
     if (n > 0 && (!b[i] || !u[i])) return fail(h, PHIPM_EINVAL, "b[i] or u[i] is NULL");
     DevProblem& P = probs[i];
     memset(&P, 0, sizeof(P));
-    P.A = make_devop(&A[i], nnz_model, nullptr);
+    P.A = make_devop(&A[i], nnz_model);
     P.p = p[i];
     P.symm = symm[i];
     P.t_end = t_end[i];
@@ -541,24 +635,14 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
     P.u = u[i];
     nmax = std::max(nmax, n);
     pmax = std::max(pmax, (int)p[i]);
-    cost[i] = (double)n * (double)(nnz_model + 1) / std::max(1, n);
+    cost[i] = (double)nnz_model + (double)n * 16.0;
   }
+  if (!assign_conversions(h, probs.data(), count, prec)) return fail(h, PHIPM_ENOMEM, "value conversion buffer");
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-  const int M1 = h->params.m_max + 1;
-  SlotLayout lay;
-  lay.ld = round_ld(nmax);
-  lay.v_off = 0;
-  lay.w_off = (long long)M1 * lay.ld * es;
-  lay.y_off = lay.w_off + (long long)(pmax + 1) * lay.ld * 8;
-  lay.e_off = lay.y_off + 2 * lay.ld * (long long)es;
-  lay.e_off = (lay.e_off + 255) & ~255ll;
-  lay.bytes = (lay.e_off + 9ll * PM_NA2 * 8 + 255) & ~255ll;   // slots stay 256-byte aligned
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f32 ? (const void*)k_solve_queue<float> : (const void*)k_solve_queue<double>,
-                                                PM_THREADS, sizeof(PmShared));
-  const int slots = std::max(1, std::min(count, std::max(1, occ) * h->num_sms));
+  const SlotLayout lay = slot_layout(nmax, pmax, h->params.m_max, es);
+  const int slots = std::max(1, std::min(count, queue_occupancy(prec) * h->num_sms));
   if (!h->ws.ensure((size_t)lay.bytes * slots)) return fail(h, PHIPM_ENOMEM, "workspace");
   const size_t pb = sizeof(DevProblem) * count, ob = sizeof(int) * count, rb = sizeof(DevResult) * count;
   if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(pb + ob) ||
@@ -574,14 +658,14 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
       (e = cudaMemsetAsync(queue, 0, sizeof(int), stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(h->res.p, 0, rb, stream)) != cudaSuccess)
     return cuda_fail(h, e, "descriptor upload");
+  if (prec != PHIPM_F64 && any_csr(probs.data(), count)) {
+    k_convert_values<<<count, 256, 0, stream>>>((const DevProblem*)h->probs.p, count, prec);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
+  }
   cudaEventRecord(h->ev0, stream);
-  if (f32)
-    k_solve_queue<float><<<slots, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, count,
-                                                                          prm, (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
-  else
-    k_solve_queue<double><<<slots, PM_THREADS, sizeof(PmShared), stream>>>((const DevProblem*)h->probs.p, (const int*)h->order.p, count,
-                                                                           prm, (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "launch");
+  e = launch_queue_any(prec, slots, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
+                       (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+  if (e != cudaSuccess) return cuda_fail(h, e, "launch");
   cudaEventRecord(h->ev1, stream);
   if ((e = cudaMemcpyAsync(h->res_host.p, h->res.p, rb, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
     return cuda_fail(h, e, "result copy");

@@ -1,10 +1,10 @@
 // Shared device-side definitions of the phipm engine: problem descriptors,
-// teams (who cooperates on one problem), bounded barriers and reductions,
-// and the float-pair arithmetic used to accumulate FP32 products at FP64
-// accuracy on the FP32 pipe.
+// teams (who cooperates on one problem), bounded barriers and reductions.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "phipm_elem.cuh"
 
 #define PM_MAXM 64
 #define PM_MAXP 8
@@ -29,9 +29,11 @@ struct DevOp {
   const int* rowptr;
   const int* colind;
   const double* val;     // CSR values, FP64 (caller's)
-  const float* valf;     // CSR values, FP32 copy (workspace; FP32 mode)
+  const float* valf;     // CSR values, FP32 copy (workspace; FP32 basis)
+  const df32* val2;      // CSR values as float pairs (workspace; float-pair basis)
   int ndim, nx, ny, nz;
   double cc, cm[3], cp[3];
+  df32 cc2, cm2[3], cp2[3];   // stencil coefficients as float pairs (hi alone for FP32)
 };
 
 struct DevParams {
@@ -125,24 +127,6 @@ struct CtaTeam {
   __device__ bool sync() const { __syncthreads(); return true; }
   static constexpr bool multi = false;
 };
-
-// ------------------------------------------------------------------------------------
-// float-pair ("double-float") accumulation: exact FP32 products summed with
-// two-sum (Knuth) into an unevaluated hi+lo pair; about 44 significant bits.
-// ------------------------------------------------------------------------------------
-struct F2Acc {
-  float hi, lo;
-};
-__device__ __forceinline__ void f2_add_prod(F2Acc& a, float x, float y) {
-  float p = x * y;
-  float e = fmaf(x, y, -p);          // x*y = p + e exactly
-  float s = a.hi + p;
-  float z = s - a.hi;
-  float t = (a.hi - (s - z)) + (p - z);
-  a.lo += t + e;
-  a.hi = s;
-}
-__device__ __forceinline__ double f2_value(const F2Acc& a) { return (double)a.hi + (double)a.lo; }
 
 // ------------------------------------------------------------------------------------
 // reductions

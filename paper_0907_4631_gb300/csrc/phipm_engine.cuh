@@ -1,58 +1,52 @@
 // The phipm method on the device (Niesen & Wright, Sec. 3), written once over
-// a "team" of CTAs that share one problem:
-//   GridTeam  every CTA of a cooperative launch; bounded grid barriers,
-//             per-CTA partial sums reduced in a fixed order (deterministic);
-//   CtaTeam   one CTA; __syncthreads.
-// S is the element type of the Krylov basis: double (FP64 mode) or float
-// (FP32 mode: basis and SpMV in FP32 with FP32 accumulation, dot products
-// accumulated as exact float products in float pairs, H / expm / eps in FP64).
-//
-// Every CTA of a team runs the same scalar code (controller, cost model) on
-// bit-identical inputs, so all CTAs take the same decisions without a broadcast.
+// a "team" of CTAs that share one problem (GridTeam: every CTA of a cooperative
+// launch; CtaTeam: one CTA) and over the element type S of the Krylov basis
+// (phipm_elem.cuh).  Every CTA of a team runs the same scalar code (controller,
+// cost model) on bit-identical inputs, so all CTAs take the same decisions
+// without a broadcast.
 #pragma once
 #include "phipm_common.cuh"
 
-// FP32 basis mode: bound on ||F|| / ||u|| per step (F = tau^p phi_p(tau A) w_p)
+// FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
 
-template <class S> struct Elem;
-template <> struct Elem<double> {
-  typedef double Acc;
-  __device__ static __forceinline__ Acc zero() { return 0.0; }
-  __device__ static __forceinline__ void dot(Acc& a, double x, double y) { a = fma(x, y, a); }
-  __device__ static __forceinline__ double val(const Acc& a) { return a; }
-  __device__ static __forceinline__ double cvt(double x) { return x; }
-  __device__ static __forceinline__ double coef(double c) { return c; }
-};
-template <> struct Elem<float> {
-  typedef F2Acc Acc;
-  __device__ static __forceinline__ Acc zero() { F2Acc a; a.hi = 0.f; a.lo = 0.f; return a; }
-  __device__ static __forceinline__ void dot(Acc& a, float x, float y) { f2_add_prod(a, x, y); }
-  __device__ static __forceinline__ double val(const Acc& a) { return f2_value(a); }
-  __device__ static __forceinline__ float cvt(double x) { return (float)x; }
-  __device__ static __forceinline__ float coef(double c) { return (float)c; }
+// Scalar state of one problem.  Thread 0 writes it, every thread reads it after
+// the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
+// would cost a warp-wide FP64 instruction per warp on a pipe of about 2 FMA/clk/SM.
+struct PmScal {
+  double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
+  double fnorm, last_tau;
+  double tl[PM_MAXP + 1];
+  df32 inv2;
+  float invf;
+  int m, m_used, kcur, invariant, sq, nonfinite, nvv, measure, outcome, status, go, symmetric, lanczos, last_m;
+  long long steps, rejects, expms;
 };
 
 // per-CTA shared state
 struct PmShared {
   double H[(PM_MAXM + 1) * PM_MAXM];   // H[i * PM_MAXM + j], Hessenberg / tridiagonal
   double red[PM_WARPS][8];
-  double coef[PM_NSLOT];               // reduced sums of the current phase
-  double h1[PM_NSLOT];                 // first Gram-Schmidt pass coefficients
-  float hf[PM_NSLOT];                  // coefficients as float (FP32 update)
+  double coef[PM_NSLOT + 2];           // reduced sums of the current phase
+  double h1[PM_NSLOT];                 // first-pass Gram-Schmidt coefficients (H = h1 + h2)
+  double hdd[PM_NSLOT];                // coefficients of the current update (FP64 basis)
+  float hf[PM_NSLOT];                  // ... as float (FP32 basis)
+  df32 hd[PM_NSLOT];                   // ... as float pairs (float-pair basis)
   double phi0[PM_NA], phi1[PM_NA];     // phi_p(tau H) e1 and phi_{p+1}(tau H) e1
   double ucoef[PM_NSLOT + PM_MAXP + 1];
-  double mat_norm;
-  double dred[PM_NSLOT + PM_WARPS];    // per-unit partial dots (vector, row chunk)
-  int ipiv[PM_NA];
-  int flag;
+  float ucf[PM_NSLOT];
+  df32 ucd[PM_NSLOT];
+  double dred[PM_NSLOT + PM_WARPS + 2];
+  double wy[PM_WARPS][PM_NA];          // per-warp column of the exponential's solve
+  PmScal sc;
 };
 
 struct PmWork {
-  double* partials;     // [2][G][PM_NSLOT] (grid team)
-  double* phi_g;        // [2][2][PM_NA]   (grid team)
-  double* expm;         // per-CTA: 8 * PM_NA2 doubles
+  double* partials;     // [2][G][PM_PSTRIDE] (grid team)
+  double* expm;         // team-shared exponential scratch: PM_EXPM_DOUBLES doubles
 };
+
+#define PM_PSTRIDE (PM_NSLOT + 2)
 
 // ------------------------------------------------------------------------------------
 // team reductions of K values held in s.coef[0..K) by each CTA
@@ -61,14 +55,14 @@ template <class Team>
 __device__ bool team_sum(const Team& team, PmShared& s, int K, const PmWork& w, int& parity) {
   if (!Team::multi) { __syncthreads(); return true; }
   const int G = team.size(), r = team.rank();
-  double* P = w.partials + (size_t)parity * G * PM_NSLOT;
+  double* P = w.partials + (size_t)parity * G * PM_PSTRIDE;
   parity ^= 1;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_NSLOT + k] = s.coef[k];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
   if (!team.sync()) return false;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = warp; k < K; k += PM_WARPS) {
     double a = 0.0;
-    for (int g = lane; g < G; g += 32) a += __ldcg(&P[(size_t)g * PM_NSLOT + k]);
+    for (int g = lane; g < G; g += 32) a += __ldcg(&P[(size_t)g * PM_PSTRIDE + k]);
     a = pm_warp_sum(a);
     if (lane == 0) s.coef[k] = a;
   }
@@ -80,14 +74,14 @@ template <class Team>
 __device__ bool team_max(const Team& team, PmShared& s, int K, const PmWork& w, int& parity) {
   if (!Team::multi) { __syncthreads(); return true; }
   const int G = team.size(), r = team.rank();
-  double* P = w.partials + (size_t)parity * G * PM_NSLOT;
+  double* P = w.partials + (size_t)parity * G * PM_PSTRIDE;
   parity ^= 1;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_NSLOT + k] = s.coef[k];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
   if (!team.sync()) return false;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = warp; k < K; k += PM_WARPS) {
     double a = -1.0;
-    for (int g = lane; g < G; g += 32) a = fmax(a, __ldcg(&P[(size_t)g * PM_NSLOT + k]));
+    for (int g = lane; g < G; g += 32) a = fmax(a, __ldcg(&P[(size_t)g * PM_PSTRIDE + k]));
     a = pm_warp_max(a);
     if (lane == 0) s.coef[k] = a;
   }
@@ -95,13 +89,13 @@ __device__ bool team_max(const Team& team, PmShared& s, int K, const PmWork& w, 
   return true;
 }
 
-// block-wide sums of 8 per-thread values into out[0..cnt)
-__device__ __forceinline__ void block_sum8(PmShared& s, double v[8], int cnt, double* out) {
+// block-wide sums of up to 8 per-thread values into out[0..cnt)
+__device__ __forceinline__ void block_sum(PmShared& s, const double* v, int cnt, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     if (k < cnt) {
-      double a = pm_warp_sum(v[k]);
+      const double a = pm_warp_sum(v[k]);
       if (lane == 0) s.red[warp][k] = a;
     }
   }
@@ -114,105 +108,140 @@ __device__ __forceinline__ void block_sum8(PmShared& s, double v[8], int cnt, do
   __syncthreads();
 }
 
-// ------------------------------------------------------------------------------------
-// SpMV rows
-// ------------------------------------------------------------------------------------
-// y_r = (A x)_r with x given by a loader functor (element index -> value of type T)
-template <class T, class XL>
-__device__ __forceinline__ T spmv_row(const DevOp& A, int r, const XL& x) {
-  if (A.kind == 0) {
-    const int k0 = __ldg(&A.rowptr[r]), k1 = __ldg(&A.rowptr[r + 1]);
-    T acc = T(0);
-    if (sizeof(T) == 8) {
-      for (int k = k0; k < k1; ++k) acc = fma((double)__ldg(&A.val[k]), (double)x(__ldg(&A.colind[k])), (double)acc);
-    } else {
-      for (int k = k0; k < k1; ++k) acc = fmaf(__ldg(&A.valf[k]), (float)x(__ldg(&A.colind[k])), (float)acc);
-    }
-    return acc;
-  }
-  const int nx = A.nx, ny = A.ny;
-  const int ix = r % nx;
-  const int iy = (r / nx) % ny;
-  const int iz = r / (nx * ny);
-  T acc = T(A.cc) * x(r);
-  if (ix > 0) acc += T(A.cm[0]) * x(r - 1);
-  if (ix < nx - 1) acc += T(A.cp[0]) * x(r + 1);
-  if (A.ndim > 1) {
-    if (iy > 0) acc += T(A.cm[1]) * x(r - nx);
-    if (iy < ny - 1) acc += T(A.cp[1]) * x(r + nx);
-  }
-  if (A.ndim > 2) {
-    const int pl = nx * ny;
-    if (iz > 0) acc += T(A.cm[2]) * x(r - pl);
-    if (iz < A.nz - 1) acc += T(A.cp[2]) * x(r + pl);
-  }
-  return acc;
+__device__ __forceinline__ void split_range(int total, int rank, int G, int& lo, int& hi) {
+  const int chunk = (total + G - 1) / G;
+  lo = min(total, rank * chunk);
+  hi = min(total, lo + chunk);
 }
 
-template <class T> struct LoadScaled {
-  const T* p; double s;
-  __device__ __forceinline__ T operator()(int i) const { return (T)((double)p[i] * s); }
+// ------------------------------------------------------------------------------------
+// SpMV: y_r = (A x)_r, x given by a loader (element index -> S)
+// ------------------------------------------------------------------------------------
+// Loads of data that other CTAs of the team wrote during this launch go through
+// L2 (ld.global.cg): the L1 of an SM is not coherent with other SMs' stores, and
+// a line cached before a team barrier could otherwise be read stale after it.
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ df32 ld_cg(const df32* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  df32 r;
+  r.hi = v.x;
+  r.lo = v.y;
+  return r;
+}
+template <class S, bool CG> struct VecLoad {
+  const S* p;
+  __device__ __forceinline__ S operator()(int i) const {
+    if constexpr (CG) return ld_cg(p + i);
+    else return p[i];
+  }
 };
-template <class T> struct LoadScaledF {    // FP32 vector times a float scale
-  const T* p; float s;
-  __device__ __forceinline__ T operator()(int i) const { return p[i] * s; }
-};
-struct LoadD {
+template <class S, bool CG> struct DLoadAs {      // FP64 vector read as S
   const double* p;
-  __device__ __forceinline__ double operator()(int i) const { return p[i]; }
+  __device__ __forceinline__ S operator()(int i) const {
+    if constexpr (CG) return Elem<S>::from_d(__ldcg(p + i));
+    else return Elem<S>::from_d(p[i]);
+  }
 };
-struct LoadDtoF {                         // FP64 vector scaled, rounded to float
-  const double* p; double s;
-  __device__ __forceinline__ float operator()(int i) const { return (float)(p[i] * s); }
-};
+
+template <class S, class XL>
+__device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
+  if constexpr (Elem<S>::kind == 0) {
+    double acc = 0.0;
+    if (A.kind == 0) {
+      const int k0 = __ldg(&A.rowptr[r]), k1 = __ldg(&A.rowptr[r + 1]);
+      for (int k = k0; k < k1; ++k) acc = fma(__ldg(&A.val[k]), x(__ldg(&A.colind[k])), acc);
+      return acc;
+    }
+    const int nx = A.nx, ny = A.ny, ix = r % nx, iy = (r / nx) % ny, iz = r / (nx * ny);
+    acc = A.cc * x(r);
+    if (ix > 0) acc = fma(A.cm[0], x(r - 1), acc);
+    if (ix < nx - 1) acc = fma(A.cp[0], x(r + 1), acc);
+    if (A.ndim > 1) {
+      if (iy > 0) acc = fma(A.cm[1], x(r - nx), acc);
+      if (iy < ny - 1) acc = fma(A.cp[1], x(r + nx), acc);
+    }
+    if (A.ndim > 2) {
+      const int pl = nx * ny;
+      if (iz > 0) acc = fma(A.cm[2], x(r - pl), acc);
+      if (iz < A.nz - 1) acc = fma(A.cp[2], x(r + pl), acc);
+    }
+    return acc;
+  } else if constexpr (Elem<S>::kind == 1) {
+    float acc = 0.f;
+    if (A.kind == 0) {
+      const int k0 = __ldg(&A.rowptr[r]), k1 = __ldg(&A.rowptr[r + 1]);
+      for (int k = k0; k < k1; ++k) acc = fmaf(__ldg(&A.valf[k]), x(__ldg(&A.colind[k])), acc);
+      return acc;
+    }
+    const int nx = A.nx, ny = A.ny, ix = r % nx, iy = (r / nx) % ny, iz = r / (nx * ny);
+    acc = A.cc2.hi * x(r);
+    if (ix > 0) acc = fmaf(A.cm2[0].hi, x(r - 1), acc);
+    if (ix < nx - 1) acc = fmaf(A.cp2[0].hi, x(r + 1), acc);
+    if (A.ndim > 1) {
+      if (iy > 0) acc = fmaf(A.cm2[1].hi, x(r - nx), acc);
+      if (iy < ny - 1) acc = fmaf(A.cp2[1].hi, x(r + nx), acc);
+    }
+    if (A.ndim > 2) {
+      const int pl = nx * ny;
+      if (iz > 0) acc = fmaf(A.cm2[2].hi, x(r - pl), acc);
+      if (iz < A.nz - 1) acc = fmaf(A.cp2[2].hi, x(r + pl), acc);
+    }
+    return acc;
+  } else {
+    F2Acc acc = f2_zero();
+    if (A.kind == 0) {
+      const int k0 = __ldg(&A.rowptr[r]), k1 = __ldg(&A.rowptr[r + 1]);
+      for (int k = k0; k < k1; ++k) {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(&A.val2[k]));
+        df32 av;
+        av.hi = a.x;
+        av.lo = a.y;
+        f2_add_prod(acc, av, x(__ldg(&A.colind[k])));
+      }
+      return f2_round(acc);
+    }
+    const int nx = A.nx, ny = A.ny, ix = r % nx, iy = (r / nx) % ny, iz = r / (nx * ny);
+    f2_add_prod(acc, A.cc2, x(r));
+    if (ix > 0) f2_add_prod(acc, A.cm2[0], x(r - 1));
+    if (ix < nx - 1) f2_add_prod(acc, A.cp2[0], x(r + 1));
+    if (A.ndim > 1) {
+      if (iy > 0) f2_add_prod(acc, A.cm2[1], x(r - nx));
+      if (iy < ny - 1) f2_add_prod(acc, A.cp2[1], x(r + nx));
+    }
+    if (A.ndim > 2) {
+      const int pl = nx * ny;
+      if (iz > 0) f2_add_prod(acc, A.cm2[2], x(r - pl));
+      if (iz < A.nz - 1) f2_add_prod(acc, A.cp2[2], x(r + pl));
+    }
+    return f2_round(acc);
+  }
+}
 
 // ------------------------------------------------------------------------------------
 // Gram-Schmidt passes over this CTA's rows [lo, hi)
 // ------------------------------------------------------------------------------------
-// d_i = sum_r V[i0+i][r] y[r], i < nv, into s.coef[0..nv).  Work is split into
-// units (vector i, row chunk c) handled by one warp each, so the cross-lane sum
-// runs once per unit rather than once per vector per warp.
-template <class S> struct Quad;
-template <> struct Quad<float> {
-  float x[4];
-  __device__ __forceinline__ void load(const float* p) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
-  }
-  __device__ __forceinline__ void store(float* p) const { *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]); }
-};
-template <> struct Quad<double> {
-  double x[4];
-  __device__ __forceinline__ void load(const double* p) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
-  }
-  __device__ __forceinline__ void store(double* p) const {
-    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
-    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
-  }
-};
-
-// d_i = sum_r V[i0+i][r] y[r], i < nv, into s.coef[0..nv).  Work is split into
-// units (vector i, row chunk c) handled by one warp each, so the cross-lane sum
-// runs once per unit rather than once per vector per warp.  lo is a multiple of
-// 64 and vectors are 256-byte aligned, so chunks start on 16-byte boundaries.
+// d_i = sum_r V[i][r] y[r], i < nv, into s.coef[0..nv); with_norm adds sum y^2
+// as s.coef[nv].  Work is split into units (vector, row chunk), one warp each,
+// so the cross-lane sum runs once per unit.  lo is a multiple of 64 and vectors
+// are 256-byte aligned, so every chunk starts on a 16-byte boundary.
 template <class S>
-__device__ void dots_cta(const S* __restrict__ V, long long ld, int i0, int nv, const S* __restrict__ y, int lo, int hi,
-                         PmShared& s) {
+__device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo, int hi,
+                         bool with_norm, PmShared& s) {
   typedef Elem<S> E;
   typedef typename E::Acc Acc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rows = hi - lo;
-  int cpv = (PM_WARPS + nv - 1) / nv;                     // chunks per vector
+  const int nvec = nv + (with_norm ? 1 : 0);
+  int cpv = (PM_WARPS + nvec - 1) / nvec;                 // chunks per vector
   cpv = max(1, min(cpv, (rows + 255) / 256));
-  const int units = nv * cpv;
+  const int units = nvec * cpv;
   const int chunk = (((rows + cpv - 1) / cpv) + 127) & ~127;
   for (int un = warp; un < units; un += PM_WARPS) {
     const int i = un / cpv, c = un - i * cpv;
     const int a = lo + c * chunk;
     const int b = min(hi, a + chunk);
-    const S* v = V + (size_t)(i0 + i) * ld;
+    const S* v = (i < nv) ? V + (size_t)i * ld : y;
     Acc acc0 = E::zero(), acc1 = E::zero();
     int e = a + 4 * lane;
     for (; e + 128 + 3 < b; e += 256) {
@@ -232,7 +261,7 @@ __device__ void dots_cta(const S* __restrict__ V, long long ld, int i0, int nv, 
     if (lane == 0) s.dred[un] = d;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
     double t = 0.0;
     for (int c = 0; c < cpv; ++c) t += s.dred[i * cpv + c];
     s.coef[i] = t;
@@ -240,72 +269,114 @@ __device__ void dots_cta(const S* __restrict__ V, long long ld, int i0, int nv, 
   __syncthreads();
 }
 
-// y[r] -= sum_{i<nv} h_i V[i][r] over this CTA's rows, four consecutive rows per
-// thread; returns this thread's sum of y[r]^2.  Element types: FP64 with FP64
-// coefficients, or FP32 with the coefficients rounded to FP32 (FP32 accumulation).
-template <class S, class C>
-__device__ __forceinline__ double update_rows(S* __restrict__ y, const S* __restrict__ V, long long ld, int nv,
-                                              const C* h, int lo, int hi) {
-  double nrm = 0.0;
+// y[r] -= sum_{i<nv} h_i V[i][r] over this CTA's rows, four consecutive rows
+// per thread (16-byte accesses).  FP64: FMA in FP64; FP32: FMA in FP32 with the
+// coefficients rounded to FP32; float pairs: the sum is accumulated as a float
+// pair and subtracted once.
+template <class S>
+__device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restrict__ V, long long ld, int nv,
+                                           const typename Elem<S>::Coef* h, int lo, int hi) {
+  typedef Elem<S> E;
   for (int r = lo + 4 * threadIdx.x; r < hi; r += 4 * blockDim.x) {
     if (r + 3 < hi) {
-      Quad<S> a, b;
+      Quad<S> a;
       a.load(y + r);
+      if constexpr (E::kind == 2) {
+        F2Acc acc[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) b.x[k] = S(0);
-      int i = 0;
-      for (; i + 1 < nv; i += 2) {
-        Quad<S> v0, v1;
-        v0.load(V + (size_t)i * ld + r);
-        v1.load(V + (size_t)(i + 1) * ld + r);
-        const S h0 = (S)h[i], h1 = (S)h[i + 1];
+        for (int k = 0; k < 4; ++k) acc[k] = f2_zero();
+        int i = 0;
+        for (; i + 1 < nv; i += 2) {
+          Quad<S> v0, v1;
+          v0.load(V + (size_t)i * ld + r);
+          v1.load(V + (size_t)(i + 1) * ld + r);
+          const df32 h0 = h[i], h1 = h[i + 1];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { a.x[k] = fma(-h0, v0.x[k], a.x[k]); b.x[k] = fma(-h1, v1.x[k], b.x[k]); }
-      }
-      if (i < nv) {
-        Quad<S> v0;
-        v0.load(V + (size_t)i * ld + r);
-        const S h0 = (S)h[i];
+          for (int k = 0; k < 4; ++k) { f2_add_prod(acc[k], h0, v0.x[k]); f2_add_prod(acc[k], h1, v1.x[k]); }
+        }
+        if (i < nv) {
+          Quad<S> v0;
+          v0.load(V + (size_t)i * ld + r);
+          const df32 h0 = h[i];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a.x[k] = fma(-h0, v0.x[k], a.x[k]);
-      }
+          for (int k = 0; k < 4; ++k) f2_add_prod(acc[k], h0, v0.x[k]);
+        }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        a.x[k] += b.x[k];
-        nrm = fma((double)a.x[k], (double)a.x[k], nrm);
+        for (int k = 0; k < 4; ++k) a.x[k] = df_sub(a.x[k], f2_round(acc[k]));
+      } else {
+        Quad<S> b;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b.x[k] = S(0);
+        int i = 0;
+        for (; i + 1 < nv; i += 2) {
+          Quad<S> v0, v1;
+          v0.load(V + (size_t)i * ld + r);
+          v1.load(V + (size_t)(i + 1) * ld + r);
+          const S h0 = h[i], h1 = h[i + 1];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) { a.x[k] = fma(-h0, v0.x[k], a.x[k]); b.x[k] = fma(-h1, v1.x[k], b.x[k]); }
+        }
+        if (i < nv) {
+          Quad<S> v0;
+          v0.load(V + (size_t)i * ld + r);
+          const S h0 = h[i];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) a.x[k] = fma(-h0, v0.x[k], a.x[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.x[k] += b.x[k];
       }
       a.store(y + r);
     } else {
       for (int q = r; q < hi; ++q) {
-        S a = y[q];
-        for (int i = 0; i < nv; ++i) a = fma(-(S)h[i], V[(size_t)i * ld + q], a);
-        y[q] = a;
-        nrm = fma((double)a, (double)a, nrm);
+        if constexpr (E::kind == 2) {
+          F2Acc acc = f2_zero();
+          for (int i = 0; i < nv; ++i) f2_add_prod(acc, h[i], V[(size_t)i * ld + q]);
+          y[q] = df_sub(y[q], f2_round(acc));
+        } else {
+          S a = y[q];
+          for (int i = 0; i < nv; ++i) a = fma(-(S)h[i], V[(size_t)i * ld + q], a);
+          y[q] = a;
+        }
       }
     }
   }
-  return nrm;
 }
 
 // ------------------------------------------------------------------------------------
-// dense kernels of one CTA on small matrices (FP64): the exponential of H_hat
+// the exponential of the augmented matrix, spread over the team's CTAs
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ void mm_cta(double* C, const double* A, const double* B, int N) {
-  const int NN = N * N;
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+#define PM_EXPM_MATS 13
+#define PM_EXPM_DOUBLES (PM_EXPM_MATS * PM_NA2 + 2 * PM_NA + PM_NA)
+
+// C = A * B on the elements [e0, e1) of the N x N result (row-major, stride PM_NA);
+// operands written by other CTAs are read through L2.
+__device__ __forceinline__ void mm_elems(double* C, const double* A, const double* B, int N, int e0, int e1) {
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N;
     const double* a = A + i * PM_NA;
-    double acc = 0.0;
-    for (int k = 0; k < N; ++k) acc = fma(a[k], B[k * PM_NA + j], acc);
-    C[i * PM_NA + j] = acc;
+    double c0 = 0.0, c1 = 0.0;
+    int k = 0;
+    for (; k + 1 < N; k += 2) {
+      c0 = fma(__ldcg(&a[k]), __ldcg(&B[k * PM_NA + j]), c0);
+      c1 = fma(__ldcg(&a[k + 1]), __ldcg(&B[(k + 1) * PM_NA + j]), c1);
+    }
+    if (k < N) c0 = fma(__ldcg(&a[k]), __ldcg(&B[k * PM_NA + j]), c0);
+    C[i * PM_NA + j] = c0 + c1;
   }
-  __syncthreads();
 }
 
-// exp(Hh) by the degree-13 Pade approximant (even/odd split) with s squarings;
-// writes the top m entries of columns ca and cb to out0/out1.
-__device__ void expm_cta(PmShared& s, double tau, int m, int p, int N, int sq, const double* bc, double* ws,
-                         int ca, int cb, double* out0, double* out1) {
+// exp(H_hat) with H_hat = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]] (Eq. hathm,
+// size N = m+p+1), degree-13 Pade approximant (even/odd split) with sq
+// squarings (Sec. 3.1).  Products are split over the team by elements; the LU
+// factorisation of the denominator runs on rank 0; the right-hand sides are
+// split by columns; only columns ca and cb of the last square are formed.
+// On return every CTA holds the top m entries of those columns in s.phi0/phi1.
+template <class Team>
+__device__ bool expm_team(const Team& team, PmShared& s, const double* bc, double tau, int m, int p, int sq,
+                          double* ws, int ca, int cb) {
+  const int N = m + p + 1, NN = N * N;
+  const int G = team.size(), rk = team.rank();
   double* X = ws;
   double* X2 = ws + 1 * PM_NA2;
   double* X4 = ws + 2 * PM_NA2;
@@ -314,10 +385,17 @@ __device__ void expm_cta(PmShared& s, double tau, int m, int p, int N, int sq, c
   double* T2 = ws + 5 * PM_NA2;
   double* U = ws + 6 * PM_NA2;
   double* Vm = ws + 7 * PM_NA2;
+  double* U2 = ws + 8 * PM_NA2;
+  double* Pm = ws + 9 * PM_NA2;
+  double* Q = ws + 10 * PM_NA2;
+  double* R = ws + 11 * PM_NA2;
+  double* R2 = ws + 12 * PM_NA2;
+  double* out = ws + PM_EXPM_MATS * PM_NA2;
+  int* piv = reinterpret_cast<int*>(out + 2 * PM_NA);
+  int e0, e1;
+  split_range(NN, rk, G, e0, e1);
   const double sc = ldexp(1.0, -sq);
-  const int NN = N * N;
-  // X = H_hat / 2^s with H_hat = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]]  (Eq. hathm, size m+p+1)
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N;
     double v = 0.0;
     if (i < m && j < m) v = tau * s.H[i * PM_MAXM + j];
@@ -325,106 +403,143 @@ __device__ void expm_cta(PmShared& s, double tau, int m, int p, int N, int sq, c
     else if (i >= m && j == i + 1) v = 1.0;
     X[i * PM_NA + j] = v * sc;
   }
+  if (!team.sync()) return false;
+  mm_elems(X2, X, X, N, e0, e1);
+  if (!team.sync()) return false;
+  mm_elems(X4, X2, X2, N, e0, e1);
+  if (!team.sync()) return false;
+  mm_elems(X6, X4, X2, N, e0, e1);
   __syncthreads();
-  (void)p;
-  mm_cta(X2, X, X, N);
-  mm_cta(X4, X2, X2, N);
-  mm_cta(X6, X4, X2, N);
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
     T1[o] = bc[13] * X6[o] + bc[11] * X4[o] + bc[9] * X2[o];
     T2[o] = bc[12] * X6[o] + bc[10] * X4[o] + bc[8] * X2[o];
   }
+  if (!team.sync()) return false;
+  mm_elems(U, X6, T1, N, e0, e1);
+  mm_elems(Vm, X6, T2, N, e0, e1);
   __syncthreads();
-  mm_cta(U, X6, T1, N);                  // U <- X6 * T1  (odd inner)
-  mm_cta(Vm, X6, T2, N);                 // V <- X6 * T2  (even)
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
     const double id = (i == j) ? 1.0 : 0.0;
-    T1[o] = U[o] + bc[7] * X6[o] + bc[5] * X4[o] + bc[3] * X2[o] + bc[1] * id;
+    U[o] = U[o] + bc[7] * X6[o] + bc[5] * X4[o] + bc[3] * X2[o] + bc[1] * id;
     Vm[o] = Vm[o] + bc[6] * X6[o] + bc[4] * X4[o] + bc[2] * X2[o] + bc[0] * id;
   }
+  if (!team.sync()) return false;
+  mm_elems(U2, X, U, N, e0, e1);     // odd part X * (...)
   __syncthreads();
-  mm_cta(U, X, T1, N);                   // U = X * (...)
-  // P = V + U -> T2 ;  Q = V - U -> X2 (reuse)
-  for (int e = threadIdx.x; e < NN; e += blockDim.x) {
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
-    T2[o] = Vm[o] + U[o];
-    X2[o] = Vm[o] - U[o];
+    Pm[o] = Vm[o] + U2[o];           // numerator
+    Q[o] = Vm[o] - U2[o];            // denominator
   }
-  __syncthreads();
-  double* Q = X2;
-  double* R = T2;
-  // LU with partial pivoting of Q; the same row swaps applied to R (= P)
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = 0; k < N; ++k) {
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = k;
-      for (int i = k + lane; i < N; i += 32) {
-        double a = fabs(Q[i * PM_NA + k]);
-        if (a > best) { best = a; bi = i; }
-      }
+  if (!team.sync()) return false;
+  // LU factorisation with partial pivoting of Q (rank 0, in place; every read of Q
+  // goes through L2 since other CTAs formed it)
+  if (rk == 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < N; ++k) {
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + lane; i < N; i += 32) {
+          const double a = fabs(__ldcg(&Q[i * PM_NA + k]));
+          if (a > best) { best = a; bi = i; }
+        }
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        for (int o = 16; o; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (bi != k)
+          for (int j = lane; j < N; j += 32) {
+            const double t = __ldcg(&Q[k * PM_NA + j]);
+            Q[k * PM_NA + j] = __ldcg(&Q[bi * PM_NA + j]);
+            Q[bi * PM_NA + j] = t;
+          }
+        __syncwarp();
+        const double pv = __ldcg(&Q[k * PM_NA + k]);
+        for (int i = k + 1 + lane; i < N; i += 32) Q[i * PM_NA + k] = __ldcg(&Q[i * PM_NA + k]) / pv;
+        if (lane == 0) piv[k] = bi;
+        __syncwarp();
       }
-      if (lane == 0) s.ipiv[k] = bi;
-    }
-    __syncthreads();
-    const int pv = s.ipiv[k];
-    if (pv != k) {
-      for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double t = Q[k * PM_NA + j]; Q[k * PM_NA + j] = Q[pv * PM_NA + j]; Q[pv * PM_NA + j] = t;
-        t = R[k * PM_NA + j]; R[k * PM_NA + j] = R[pv * PM_NA + j]; R[pv * PM_NA + j] = t;
+      __syncthreads();
+      const int w = N - k - 1;
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int i = k + 1 + e / w, j = k + 1 + e % w;
+        Q[i * PM_NA + j] = fma(-__ldcg(&Q[i * PM_NA + k]), __ldcg(&Q[k * PM_NA + j]), __ldcg(&Q[i * PM_NA + j]));
       }
       __syncthreads();
     }
-    const double piv = Q[k * PM_NA + k];
-    for (int i = k + 1 + threadIdx.x; i < N; i += blockDim.x) Q[i * PM_NA + k] /= piv;
-    __syncthreads();
-    const int rows = N - k - 1;
-    const int tot = rows * (2 * N - k - 1);   // trailing Q block (rows x (N-k-1)) and R rows (rows x N)
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int i = k + 1 + e / (2 * N - k - 1);
-      const int c = e % (2 * N - k - 1);
-      const double l = Q[i * PM_NA + k];
-      if (c < N - k - 1) {
-        const int j = k + 1 + c;
-        Q[i * PM_NA + j] = fma(-l, Q[k * PM_NA + j], Q[i * PM_NA + j]);
-      } else {
-        const int j = c - (N - k - 1);
-        R[i * PM_NA + j] = fma(-l, R[k * PM_NA + j], R[i * PM_NA + j]);
+  }
+  if (!team.sync()) return false;
+  // R = Q^{-1} P, one warp per column, columns split over the team
+  {
+    int c0, c1;
+    split_range(N, rk, G, c0, c1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* yv = s.wy[warp];
+    for (int j = c0 + warp; j < c1; j += PM_WARPS) {
+      for (int i = lane; i < N; i += 32) yv[i] = __ldcg(&Pm[i * PM_NA + j]);
+      __syncwarp();
+      if (lane == 0)
+        for (int k = 0; k < N; ++k) {
+          const int pk = __ldcg(&piv[k]);
+          if (pk != k) { const double t = yv[k]; yv[k] = yv[pk]; yv[pk] = t; }
+        }
+      __syncwarp();
+      for (int i = 1; i < N; ++i) {          // unit lower triangular
+        double a = 0.0;
+        for (int k = lane; k < i; k += 32) a = fma(__ldcg(&Q[i * PM_NA + k]), yv[k], a);
+        a = pm_warp_sum(a);
+        if (lane == 0) yv[i] -= a;
+        __syncwarp();
       }
+      for (int i = N - 1; i >= 0; --i) {     // upper triangular
+        double a = 0.0;
+        for (int k = i + 1 + lane; k < N; k += 32) a = fma(__ldcg(&Q[i * PM_NA + k]), yv[k], a);
+        a = pm_warp_sum(a);
+        if (lane == 0) yv[i] = (yv[i] - a) / __ldcg(&Q[i * PM_NA + i]);
+        __syncwarp();
+      }
+      for (int i = lane; i < N; i += 32) R[i * PM_NA + j] = yv[i];
+      __syncwarp();
     }
-    __syncthreads();
   }
-  // back substitution U R = (L^{-1} P R) column-parallel over all N columns
-  for (int k = N - 1; k >= 0; --k) {
-    const double d = Q[k * PM_NA + k];
-    for (int j = threadIdx.x; j < N; j += blockDim.x) R[k * PM_NA + j] /= d;
-    __syncthreads();
-    const int tot = k * N;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int i = e / N, j = e - i * N;
-      R[i * PM_NA + j] = fma(-Q[i * PM_NA + k], R[k * PM_NA + j], R[i * PM_NA + j]);
-    }
-    __syncthreads();
-  }
-  // squarings
+  if (!team.sync()) return false;
+  // squarings; the last one forms only columns ca and cb
   double* cur = R;
-  double* oth = U;
-  for (int q = 0; q < sq; ++q) {
-    mm_cta(oth, cur, cur, N);
+  double* oth = R2;
+  for (int q = 0; q + 1 < sq; ++q) {
+    mm_elems(oth, cur, cur, N, e0, e1);
+    if (!team.sync()) return false;
     double* t = cur; cur = oth; oth = t;
   }
+  {
+    int r0, r1;
+    split_range(2 * N, rk, G, r0, r1);
+    for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+      const int which = e / N, i = e - which * N;
+      const int col = which ? cb : ca;
+      double v;
+      if (sq == 0) {
+        v = __ldcg(&cur[i * PM_NA + col]);
+      } else {
+        double c0 = 0.0;
+        for (int k = 0; k < N; ++k) c0 = fma(__ldcg(&cur[i * PM_NA + k]), __ldcg(&cur[k * PM_NA + col]), c0);
+        v = c0;
+      }
+      out[which * PM_NA + i] = v;
+    }
+  }
+  if (!team.sync()) return false;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    out0[i] = cur[i * PM_NA + ca];
-    out1[i] = cur[i * PM_NA + cb];
+    s.phi0[i] = __ldcg(&out[i]);
+    s.phi1[i] = __ldcg(&out[PM_NA + i]);
   }
   __syncthreads();
+  return true;
 }
 
 __device__ __forceinline__ int pm_squarings(double norm1, double theta) {
@@ -436,17 +551,43 @@ __device__ __forceinline__ int pm_squarings(double norm1, double theta) {
 // ------------------------------------------------------------------------------------
 // the solver
 // ------------------------------------------------------------------------------------
-struct Ctl {   // controller memory of Algorithm 4 within one step
+struct Ctl {   // controller memory of Algorithm 4 within one step (thread 0 only)
   bool rejected, tau_changed, m_changed, qf, kf;
   double q, kap, eps_old, tau_old;
   int m_old;
 };
 
+__device__ __forceinline__ void ctl_reset(Ctl& c) {
+  c.rejected = c.tau_changed = c.m_changed = c.qf = c.kf = false;
+  c.q = 0.0; c.kap = 2.0; c.eps_old = 0.0; c.tau_old = 0.0; c.m_old = 0;
+}
+
+template <class S> __device__ __forceinline__ typename Elem<S>::Coef* coef_array(PmShared& s);
+template <> __device__ __forceinline__ double* coef_array<double>(PmShared& s) { return s.hdd; }
+template <> __device__ __forceinline__ float* coef_array<float>(PmShared& s) { return s.hf; }
+template <> __device__ __forceinline__ df32* coef_array<df32>(PmShared& s) { return s.hd; }
+template <class S> __device__ __forceinline__ typename Elem<S>::Coef scal_inv(const PmScal& c);
+template <> __device__ __forceinline__ double scal_inv<double>(const PmScal& c) { return c.inv; }
+template <> __device__ __forceinline__ float scal_inv<float>(const PmScal& c) { return c.invf; }
+template <> __device__ __forceinline__ df32 scal_inv<df32>(const PmScal& c) { return c.inv2; }
+
+__device__ __forceinline__ void set_inv(PmScal& c, double x) {   // thread 0: 1/x in every form
+  c.inv = 1.0 / x;
+  c.invf = (float)c.inv;
+  c.inv2 = df_from_d(c.inv);
+}
+
+// Algorithm 3's attempt outcome after the controller (thread 0 decides)
+#define PM_ATT_RETRY 0     // non-finite estimate or FP32 guard: try again with a smaller tau
+#define PM_ATT_REJECT 1    // omega > delta
+#define PM_ATT_ACCEPT 2    // omega <= delta
+#define PM_ATT_FAIL 3      // status set
+
 template <class Team, class S>
 __device__ void phipm_device(const Team& team, const DevProblem& P, const DevParams& prm, DevResult& res,
-                             PmShared& s, const PmWork& w, double* expm_ws) {
+                             PmShared& s, const PmWork& w) {
   typedef Elem<S> E;
-  typedef typename E::Acc Acc;
+  typedef typename E::Coef C;
   const int n = P.A.n, p = P.p;
   const int tid = threadIdx.x, nth = blockDim.x;
   int lo, hi;
@@ -457,19 +598,26 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   double* W = P.W;
   double* u = P.u;                        // current solution u(t_k)
   double* ualt = P.W + (size_t)p * P.ld;  // spare vector (FP32 guard)
+  C* hc = coef_array<S>(s);               // coefficients of the current update, as S needs them
+  PmScal& c = s.sc;                       // scalar state: written by thread 0, read after a barrier
   int parity = 0;
-  int status = PM_OK;
-  long long steps = 0, rejects = 0, matvecs = 0, expms = 0, kry_steps = 0, gs_vectors = 0;
-  double err_sum = 0.0;
-  double r_normA = 0.0, r_normb = 0.0, r_last_tau = 0.0;
-  int r_last_m = 0;
-  bool symmetric = false;
-  for (int e = threadIdx.x; e < (PM_MAXM + 1) * PM_MAXM; e += blockDim.x) s.H[e] = 0.0;
+  long long matvecs = 0, kry_steps = 0, gs_vectors = 0;
+  Ctl ctl;                                // thread 0's controller memory
+  ctl_reset(ctl);
+  for (int e = tid; e < (PM_MAXM + 1) * PM_MAXM; e += nth) s.H[e] = 0.0;
+  if (tid == 0) {
+    c.status = PM_OK;
+    c.steps = c.rejects = c.expms = 0;
+    c.err_sum = 0.0;
+    c.normA = c.normb = c.last_tau = 0.0;
+    c.last_m = 0;
+    c.symmetric = 0;
+  }
   __syncthreads();
 
-#define PM_SYNC_OR_FAIL() do { if (!team.sync()) { status = PM_ETIMEOUT; goto done; } } while (0)
-#define PM_SUM_OR_FAIL(K) do { if (!team_sum(team, s, (K), w, parity)) { status = PM_ETIMEOUT; goto done; } } while (0)
-#define PM_MAX_OR_FAIL(K) do { if (!team_max(team, s, (K), w, parity)) { status = PM_ETIMEOUT; goto done; } } while (0)
+#define PM_SYNC_OR_FAIL() do { if (!team.sync()) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
+#define PM_SUM_OR_FAIL(K) do { if (!team_sum(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
+#define PM_MAX_OR_FAIL(K) do { if (!team_max(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 
   // ---------------- setup (a1): ||A||_inf, ||b_0||_inf, max_k ||b_k||_inf, symmetry; u = b_0
   {
@@ -482,8 +630,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           const double a = P.A.val[k];
           rs += fabs(a);
           if (P.symm < 0) {       // look for the transposed entry in row colind[k]
-            const int c = P.A.colind[k];
-            const int q0 = P.A.rowptr[c], q1 = P.A.rowptr[c + 1];
+            const int cc = P.A.colind[k];
+            const int q0 = P.A.rowptr[cc], q1 = P.A.rowptr[cc + 1];
             bool found = false;
             for (int q = q0; q < q1; ++q)
               if (P.A.colind[q] == r) { found = true; if (P.A.val[q] != a) asym = 1.0; }
@@ -499,18 +647,17 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       u[r] = P.b[0][r];
     }
     const double t0 = pm_warp_max(na), t1 = pm_warp_max(nb0), t2 = pm_warp_max(nball), t3 = pm_warp_max(asym);
-    __shared__ double red4[PM_WARPS][4];
-    if ((tid & 31) == 0) { red4[tid >> 5][0] = t0; red4[tid >> 5][1] = t1; red4[tid >> 5][2] = t2; red4[tid >> 5][3] = t3; }
+    if ((tid & 31) == 0) { s.red[tid >> 5][0] = t0; s.red[tid >> 5][1] = t1; s.red[tid >> 5][2] = t2; s.red[tid >> 5][3] = t3; }
     __syncthreads();
     if (tid < 4) {
       double a = 0.0;
-      for (int q = 0; q < PM_WARPS; ++q) a = fmax(a, red4[q][tid]);
+      for (int q = 0; q < PM_WARPS; ++q) a = fmax(a, s.red[q][tid]);
       s.coef[tid] = a;
     }
     __syncthreads();
     PM_MAX_OR_FAIL(4);
   }
-  {
+  if (tid == 0) {
     double normA;
     if (P.A.kind == 0) {
       normA = s.coef[0];
@@ -519,388 +666,403 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       for (int d = 0; d < P.A.ndim; ++d) normA += fabs(P.A.cm[d]) + fabs(P.A.cp[d]);
     }
     double normb = s.coef[1];
-    const double normb_all = s.coef[2];
+    bool symmetric;
     if (P.symm >= 0) symmetric = P.symm != 0;
     else if (P.A.kind == 0) symmetric = s.coef[3] == 0.0;
     else {
       symmetric = true;
       for (int d = 0; d < P.A.ndim; ++d) symmetric = symmetric && (P.A.cm[d] == P.A.cp[d]);
     }
-    if (normb == 0.0) normb = normb_all;
-    r_normA = normA;
-    r_normb = normb;
-    if (n == 0 || normb == 0.0) {        // every b_k = 0: u = 0
-      for (int r = lo + tid; r < hi; r += nth) u[r] = 0.0;
-      goto done;
-    }
-    const double tol = P.tol > 0.0 ? P.tol : 1e-7;
-    const double t_end = P.t_end;
-    const int m_max = prm.m_max;
-    int m = min(prm.m_init, m_max);
-    const double bd_abs = prm.breakdown_tol * fmax(normA, 2.2250738585072014e-308);
-    double tau;
+    if (normb == 0.0) normb = s.coef[2];
+    c.normA = normA;
+    c.normb = normb;
+    c.symmetric = symmetric ? 1 : 0;
+    // Lanczos (Algorithm 2) for symmetric A with an FP64-class basis; the FP32
+    // basis always uses full CGS2 (the three-term recurrence loses orthogonality)
+    c.lanczos = (symmetric && E::kind != 1) ? 1 : 0;
+    c.go = (n > 0 && normb > 0.0) ? 1 : 0;
+    c.tol = P.tol > 0.0 ? P.tol : 1e-7;
+    c.t_end = P.t_end;
+    c.m = min(prm.m_init, prm.m_max);
+    c.bd_abs = prm.breakdown_tol * fmax(normA, 2.2250738585072014e-308);
     if (normA == 0.0) {
-      tau = t_end;
+      c.tau = c.t_end;
     } else {       // Eq. (tau_0) in logarithms, m_bar = (m_init + m_max)/2
-      const double mb = 0.5 * (prm.m_init + m_max);
-      const double lg = log(tol) + (mb + 1.0) * (log(mb + 1.0) - 1.0) + 0.5 * log(2.0 * 3.141592653589793 * (mb + 1.0)) -
-                        log(4.0 * normA * normb);
-      tau = fmin(10.0 / normA * exp(lg / mb), t_end);
+      const double mb = 0.5 * (prm.m_init + prm.m_max);
+      const double lg = log(c.tol) + (mb + 1.0) * (log(mb + 1.0) - 1.0) +
+                        0.5 * log(2.0 * 3.141592653589793 * (mb + 1.0)) - log(4.0 * normA * normb);
+      c.tau = fmin(10.0 / normA * exp(lg / mb), c.t_end);
     }
-    const long long nnzA = P.A.nnz;
-    PM_SYNC_OR_FAIL();          // u = b_0 complete before the first SpMV
+    c.t = 0.0;
+    c.nonfinite = 0;
+  }
+  __syncthreads();
+  if (!c.go) {        // every b_k = 0: u = 0
+    for (int r = lo + tid; r < hi; r += nth) u[r] = 0.0;
+    goto done;
+  }
+  PM_SYNC_OR_FAIL();  // u = b_0 complete before the first SpMV
 
-    double t = 0.0;
-    int nonfinite = 0;
-    while (t < t_end) {
-      // ---------------- w-recurrence (a2), Eq. (wrecurrence): p SpMVs in FP64
-      double beta, unorm;
-      {
-        double tl[PM_MAXP + 1];
-        tl[0] = 1.0;
-        for (int l = 1; l <= p; ++l) tl[l] = tl[l - 1] * t / (double)l;
-        for (int j = 1; j <= p; ++j) {
-          const double* xin = (j == 1) ? u : W + (size_t)(j - 2) * ld;
-          double* wout = W + (size_t)(j - 1) * ld;
-          double nrm = 0.0;
-          LoadD xl{xin};
-          for (int r = lo + tid; r < hi; r += nth) {
-            double y = spmv_row<double>(P.A, r, xl);
-            for (int l = 0; l <= p - j; ++l) y = fma(tl[l], P.b[j + l][r], y);
-            wout[r] = y;
-            if (j == p) nrm = fma(y, y, nrm);
-          }
-          matvecs += 1;
-          if (j == p) {
-            double un = 0.0;
-            for (int r = lo + tid; r < hi; r += nth) un = fma(u[r], u[r], un);
-            double v[8] = {nrm, un, 0, 0, 0, 0, 0, 0};
-            block_sum8(s, v, 2, s.coef);
-            PM_SUM_OR_FAIL(2);
-          } else {
-            PM_SYNC_OR_FAIL();
-          }
-        }
-        if (p == 0) {
-          double nrm = 0.0;
-          for (int r = lo + tid; r < hi; r += nth) nrm = fma(u[r], u[r], nrm);
-          double v[8] = {nrm, nrm, 0, 0, 0, 0, 0, 0};
-          block_sum8(s, v, 2, s.coef);
-          PM_SUM_OR_FAIL(2);
-        }
-        beta = sqrt(s.coef[0]);
-        unorm = sqrt(s.coef[1]);
+  while (c.t < c.t_end) {
+    // ---------------- w-recurrence (a2), Eq. (wrecurrence): p SpMVs in FP64
+    if (tid == 0) {
+      c.tl[0] = 1.0;
+      for (int l = 1; l <= p; ++l) c.tl[l] = c.tl[l - 1] * c.t / (double)l;
+    }
+    __syncthreads();
+    for (int j = 1; j <= p; ++j) {
+      const double* xin = (j == 1) ? u : W + (size_t)(j - 2) * ld;
+      double* wout = W + (size_t)(j - 1) * ld;
+      double nrm = 0.0;
+      VecLoad<double, Team::multi> xl{xin};
+      for (int r = lo + tid; r < hi; r += nth) {
+        double y = spmv_row<double>(P.A, r, xl);
+        for (int l = 0; l <= p - j; ++l) y = fma(c.tl[l], P.b[j + l][r], y);
+        wout[r] = y;
+        if (j == p) nrm = fma(y, y, nrm);
       }
-      const double* wp = (p == 0) ? u : W + (size_t)(p - 1) * ld;
-      int kcur = 0;            // Arnoldi / Lanczos steps done for this w_p
-      bool invariant = false;  // happy breakdown reached
-      double ynorm_last = 0.0; // ||y|| of the last step (h_{kcur+1,kcur})
-      Ctl ctl;
-      ctl.rejected = ctl.tau_changed = ctl.m_changed = ctl.qf = ctl.kf = false;
-      ctl.q = 0.0; ctl.kap = 2.0; ctl.eps_old = 0.0; ctl.tau_old = 0.0; ctl.m_old = 0;
-      bool accepted = false;
-      while (!accepted) {
-        const double tau_used = tau;
-        int m_used = m;
-        double eps = 0.0, hlast = 0.0;
-        int sq = 0;
-        double norm1 = (p > 0) ? 1.0 : 0.0;
-        if (beta > 0.0) {
-          // ---------------- Krylov extension (a3/a4) to m steps
-          const int target = invariant ? kcur : m;
-          if (kcur < target) {
-            const int j0 = kcur;       // first step of this extension
-            for (int j = j0; j < target; ++j) {
-              // phase A: x = v_j ; y = A x ; first-pass dots
-              if (j == 0) {
-                const double inv = 1.0 / beta;
-                for (int r = lo + tid; r < hi; r += nth) V[r] = E::cvt(wp[r] * inv);
-              } else if (j == j0) {
-                // v_j already normalised in V[j] by the end of the previous extension
-              } else {
-                const S* yprev = Y + (size_t)((j - 1) & 1) * ld;
-                const double inv = 1.0 / ynorm_last;
-                for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::cvt((double)yprev[r] * inv);
-              }
-              __syncthreads();
-              S* ycur = Y + (size_t)(j & 1) * ld;
-              if (j == 0) {
-                if (sizeof(S) == 8) {
-                  LoadScaled<double> xl{wp, 1.0 / beta};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<double>(P.A, r, xl);
-                } else {
-                  LoadDtoF xl{wp, 1.0 / beta};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<float>(P.A, r, xl);
-                }
-              } else if (j == j0) {
-                const S* xv = V + (size_t)j * ld;
-                if (sizeof(S) == 8) {
-                  LoadD xl{(const double*)xv};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<double>(P.A, r, xl);
-                } else {
-                  LoadScaledF<float> xl{(const float*)xv, 1.0f};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<float>(P.A, r, xl);
-                }
-              } else {
-                const S* yprev = Y + (size_t)((j - 1) & 1) * ld;
-                if (sizeof(S) == 8) {
-                  LoadScaled<double> xl{(const double*)yprev, 1.0 / ynorm_last};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<double>(P.A, r, xl);
-                } else {
-                  LoadScaledF<float> xl{(const float*)yprev, (float)(1.0 / ynorm_last)};
-                  for (int r = lo + tid; r < hi; r += nth) ycur[r] = (S)spmv_row<float>(P.A, r, xl);
-                }
-              }
-              matvecs += 1;
-              kry_steps += 1;
-              __syncthreads();
-              const bool lanczos = symmetric && sizeof(S) == 8;
-              if (!lanczos) gs_vectors += j + 1;
-              const int i0 = lanczos ? j : 0;          // Lanczos: only t_jj = v_j^T y here
-              const int nv = j + 1 - i0;
-              // dots d_i = v_i . y over my rows
-              dots_cta<S>(V, ld, i0, nv, ycur, lo, hi, s);
-              PM_SUM_OR_FAIL(nv);
-              if (lanczos) {
-                // Algorithm 2: y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
-                const double tjj = s.coef[0];
-                const double tjm = (j > 0) ? s.H[(j - 1) * PM_MAXM + j] : 0.0;
-                __syncthreads();
-                double nrm = 0.0;
-                for (int r = lo + tid; r < hi; r += nth) {
-                  double y = (double)ycur[r];
-                  if (j > 0) y = fma(-tjm, (double)V[(size_t)(j - 1) * ld + r], y);
-                  y = fma(-tjj, (double)V[(size_t)j * ld + r], y);
-                  ycur[r] = (S)y;
-                  nrm = fma(y, y, nrm);
-                }
-                double v[8] = {nrm, 0, 0, 0, 0, 0, 0, 0};
-                block_sum8(s, v, 1, s.coef);
-                PM_SUM_OR_FAIL(1);
-                const double hn = sqrt(s.coef[0]);
-                if (tid == 0) {
-                  s.H[j * PM_MAXM + j] = tjj;
-                  if (j + 1 < PM_MAXM + 1) s.H[(j + 1) * PM_MAXM + j] = hn;
-                  if (j + 1 < PM_MAXM) s.H[j * PM_MAXM + j + 1] = hn;
-                  if (j > 0) s.H[(j - 1) * PM_MAXM + j] = tjm;
-                }
-                __syncthreads();
-                ynorm_last = hn;
-              } else {
-                // CGS2: y -= V h1 ; h2 = V^T y ; y -= V h2 ; h = h1 + h2
-                for (int k = tid; k < nv; k += nth) { s.h1[k] = s.coef[k]; s.hf[k] = E::coef(s.coef[k]); }
-                __syncthreads();
-                for (int pass = 0; pass < 2; ++pass) {
-                  double nrm;
-                  if (sizeof(S) == 8) nrm = update_rows<S, double>(ycur, V, ld, nv, s.h1, lo, hi);
-                  else nrm = update_rows<S, float>(ycur, V, ld, nv, s.hf, lo, hi);
-                  __syncthreads();
-                  if (pass == 0) {
-                    dots_cta<S>(V, ld, 0, nv, ycur, lo, hi, s);
-                    PM_SUM_OR_FAIL(nv);
-                    for (int k = tid; k < nv; k += nth) {
-                      const double h2 = s.coef[k];
-                      s.H[k * PM_MAXM + j] = s.h1[k] + h2;
-                      s.h1[k] = h2;
-                      s.hf[k] = E::coef(h2);
-                    }
-                    __syncthreads();
-                  } else {
-                    double v[8] = {nrm, 0, 0, 0, 0, 0, 0, 0};
-                    block_sum8(s, v, 1, s.coef);
-                    PM_SUM_OR_FAIL(1);
-                  }
-                }
-                const double hn = sqrt(s.coef[0]);
-                if (tid == 0) s.H[(j + 1) * PM_MAXM + j] = hn;
-                __syncthreads();
-                ynorm_last = hn;
-              }
-              if (ynorm_last <= bd_abs) {      // happy breakdown (R12): invariant subspace
-                if (tid == 0) s.H[(j + 1) * PM_MAXM + j] = 0.0;
-                __syncthreads();
-                ynorm_last = 0.0;
-                invariant = true;
-                kcur = j + 1;
-                break;
-              }
-              kcur = j + 1;
+      matvecs += 1;
+      if (j == p) {
+        const double v[1] = {nrm};
+        block_sum(s, v, 1, s.coef);
+        PM_SUM_OR_FAIL(1);
+      } else {
+        PM_SYNC_OR_FAIL();
+      }
+    }
+    if (p == 0) {
+      double nrm = 0.0;
+      for (int r = lo + tid; r < hi; r += nth) nrm = fma(u[r], u[r], nrm);
+      const double v[1] = {nrm};
+      block_sum(s, v, 1, s.coef);
+      PM_SUM_OR_FAIL(1);
+    }
+    if (tid == 0) {
+      c.beta = sqrt(s.coef[0]);
+      if (c.beta > 0.0) set_inv(c, c.beta);
+      c.kcur = 0;          // Arnoldi / Lanczos steps done for this w_p
+      c.invariant = 0;     // happy breakdown reached
+      c.hn = 0.0;          // ||y|| of the last step (h_{kcur+1,kcur})
+      ctl_reset(ctl);
+    }
+    __syncthreads();
+    const double* wp = (p == 0) ? u : W + (size_t)(p - 1) * ld;
+    for (;;) {   // attempts of one step (Algorithm 3, inner loop)
+      if (tid == 0) {
+        c.tau_used = c.tau;
+        c.m_used = c.m;
+        c.eps = 0.0;
+        c.hlast = 0.0;
+        c.sq = 0;
+        c.norm1 = (p > 0) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      if (c.beta > 0.0) {
+        // ---------------- Krylov extension (a3/a4) to m steps
+        const int target = c.invariant ? c.kcur : c.m;
+        const int j0 = c.kcur;   // first step of this extension
+        if (j0 < target) {
+          for (int j = j0; j < target; ++j) {
+            // phase A: write v_j (my rows), y = A v_j
+            S* ycur = Y + (size_t)(j & 1) * ld;
+            const S* yprev = Y + (size_t)((j + 1) & 1) * ld;
+            const C sc = scal_inv<S>(c);   // 1/beta at j = 0, else 1/||y_{j-1}||
+            if (j == 0) {
+              for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
+              DLoadAs<S, Team::multi> xl{wp};
+              for (int r = lo + tid; r < hi; r += nth) ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+            } else if (j == j0) {
+              VecLoad<S, Team::multi> xl{V + (size_t)j * ld};   // v_j normalised at the end of the previous extension
+              for (int r = lo + tid; r < hi; r += nth) ycur[r] = spmv_row<S>(P.A, r, xl);
+            } else {
+              for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
+              VecLoad<S, Team::multi> xl{yprev};
+              for (int r = lo + tid; r < hi; r += nth) ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
             }
-            // normalise the last vector: v_{kcur} = y / ||y||  (my rows)
-            if (ynorm_last > 0.0) {
-              const S* yl = Y + (size_t)((kcur - 1) & 1) * ld;
-              const double inv = 1.0 / ynorm_last;
-              for (int r = lo + tid; r < hi; r += nth) V[(size_t)kcur * ld + r] = E::cvt((double)yl[r] * inv);
-            }
-          }
-          m_used = min(m, kcur);
-          hlast = s.H[m_used * PM_MAXM + m_used - 1];
-          if (invariant && m_used == kcur) hlast = 0.0;
-          // ---------------- augmented matrix (Eq. hathm + R2) and its exponential (a5)
-          const int N = m_used + p + 1;
-          // ||H_hat||_1 = max(tau ||H_m||_1, 1): the augmented columns each hold a single 1
-          if (tid < 32) {
-            double mx = 0.0;
-            for (int jj = tid; jj < m_used; jj += 32) {
-              double cs = 0.0;
-              for (int i = 0; i < m_used; ++i) cs += fabs(s.H[i * PM_MAXM + jj]);
-              mx = fmax(mx, tau_used * cs);
-            }
-            mx = pm_warp_max(mx);
-            if (tid == 0) s.mat_norm = fmax(mx, 1.0);
-          }
-          __syncthreads();
-          norm1 = s.mat_norm;
-          sq = pm_squarings(norm1, prm.theta13);
-          const int ca = (p >= 1) ? m_used + p - 1 : 0;
-          const int cb = m_used + p;
-          if (Team::multi) {
-            double* pg = w.phi_g + (size_t)(expms & 1) * 2 * PM_NA;
-            if (team.rank() == 0) expm_cta(s, tau_used, m_used, p, N, sq, prm.pade_b, expm_ws, ca, cb, pg, pg + PM_NA);
-            PM_SYNC_OR_FAIL();
-            for (int i = tid; i < m_used; i += nth) { s.phi0[i] = __ldcg(&pg[i]); s.phi1[i] = __ldcg(&pg[PM_NA + i]); }
+            matvecs += 1;
+            kry_steps += 1;
             __syncthreads();
-          } else {
-            expm_cta(s, tau_used, m_used, p, N, sq, prm.pade_b, expm_ws, ca, cb, s.phi0, s.phi1);
-          }
-          expms += 1;
-          // ---------------- error estimate (a6), Eq. (errest) with R4
-          eps = pow(tau_used, p + 1) * beta * fabs(hlast) * fabs(s.phi1[m_used - 1]);
-        } else {
-          m_used = m;
-        }
-        if (!isfinite(eps)) {
-          nonfinite += 1;
-          rejects += 1;
-          if (nonfinite >= 10) { status = PM_ENONFINITE; goto done; }
-          tau = tau / 5.0;
-          ctl.rejected = ctl.tau_changed = ctl.m_changed = ctl.qf = ctl.kf = false;
-          continue;
-        }
-        nonfinite = 0;
-        m = m_used;
-        // ---------------- controller (a7): Eq. (taunew), Algorithm 4, Eqs. (2)-(8)
-        const double omega = t_end * eps / (tau_used * tol);
-        double q;
-        bool qf;
-        if (ctl.rejected && ctl.tau_changed) {
-          q = (eps > 0.0 && ctl.eps_old > 0.0 && tau_used != ctl.tau_old)
-                  ? log(eps / ctl.eps_old) / log(tau_used / ctl.tau_old) - 1.0 : nan("");
-          if (!isfinite(q)) { q = m / 4.0; qf = false; }
-          else { q = fmin(fmax(q, 0.0), (double)m); qf = true; }
-        } else if (ctl.rejected && ctl.qf) {
-          q = ctl.q; qf = true;
-        } else {
-          q = m / 4.0; qf = false;
-        }
-        ctl.q = q; ctl.qf = qf;
-        const double tau_new = (omega > 0.0) ? tau_used * pow(prm.gamma / omega, 1.0 / (q + 1.0)) : INFINITY;
-        double kap;
-        bool kf;
-        if (ctl.rejected && ctl.m_changed) {
-          kap = (eps > 0.0 && ctl.eps_old > 0.0 && m != ctl.m_old)
-                    ? pow(eps / ctl.eps_old, 1.0 / (double)(ctl.m_old - m)) : nan("");
-          if (!isfinite(kap) || kap <= 1.0) { kap = 2.0; kf = false; }
-          else kf = true;
-        } else if (ctl.rejected && ctl.kf) {
-          kap = ctl.kap; kf = true;
-        } else {
-          kap = 2.0; kf = false;
-        }
-        ctl.kap = kap; ctl.kf = kf;
-        const double m_new_real = (omega > 0.0) ? m + log(omega / prm.gamma) / log(kap) : -INFINITY;
-        int m_new;
-        if (isfinite(m_new_real)) {
-          const double c = fmin(fmax(ceil(m_new_real), 1.0), (double)m_max);
-          m_new = (int)c;
-        } else {
-          m_new = (m_new_real < 0.0) ? 1 : m_max;
-        }
-        const double Mf = 44.0 / 3.0 + 2.0 * pm_squarings(norm1, prm.theta13);
-        const double t_left = t_end - t;
-        auto C1 = [&](double mm) {
-          if (symmetric) return (mm + p) * (double)nnzA + 3.0 * (mm + p) * n + Mf * (mm + p + 1) * (mm + p + 1) * (mm + p + 1);
-          return (mm + p) * (double)nnzA + (mm * mm + 3 * p + 2) * (double)n + Mf * (mm + p + 1) * (mm + p + 1) * (mm + p + 1);
-        };
-        const double c_tau = ceil(t_left / tau_new) * C1((double)m);
-        const double c_m = ceil(t_left / tau_used) * C1((double)m_new);
-        bool branch_tau;
-        if (c_tau < c_m) {
-          tau = fmin(fmin(fmax(tau_new, tau_used / 5.0), 2.0 * tau_used), t_left);
-          branch_tau = true;
-        } else {
-          int mm = max(max(m_new, (3 * m) / 4), 1);
-          mm = min(min(mm, (4 * m + 2) / 3), m_max);
-          m = mm;
-          branch_tau = false;
-        }
-        if (omega <= prm.delta) {
-          // ---------------- accept: Eq. (step) (a8), F by Eq. (phipapprox2)
-          if (tid == 0) {
-            const double tp = pow(tau_used, p);
-            if (beta > 0.0) {
-              for (int i = 0; i < m_used; ++i) s.ucoef[i] = tp * beta * s.phi0[i];
-              s.ucoef[m_used] = (hlast != 0.0) ? tp * tau_used * beta * hlast * s.phi1[m_used - 1] : 0.0;
+            if (c.lanczos) {
+              // Algorithm 2: t_jj = v_j^T y ; y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
+              dots_cta<S>(V + (size_t)j * ld, ld, 1, ycur, lo, hi, false, s);
+              PM_SUM_OR_FAIL(1);
+              if (tid == 0) {
+                const double tjj = s.coef[0];
+                s.H[j * PM_MAXM + j] = tjj;
+                if (j > 0) { hc[0] = E::coef(s.H[(j - 1) * PM_MAXM + j]); hc[1] = E::coef(tjj); }
+                else hc[0] = E::coef(tjj);
+              }
+              __syncthreads();
+              if (j > 0) update_rows<S>(ycur, V + (size_t)(j - 1) * ld, ld, 2, hc, lo, hi);
+              else update_rows<S>(ycur, V, ld, 1, hc, lo, hi);
+              __syncthreads();
+              dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
+              PM_SUM_OR_FAIL(1);
+              if (tid == 0) {
+                const double hn = sqrt(s.coef[0]);
+                s.H[(j + 1) * PM_MAXM + j] = hn;
+                if (j + 1 < PM_MAXM) s.H[j * PM_MAXM + j + 1] = hn;
+                c.hn = hn;
+              }
+            } else {
+              // CGS2: h1 = V^T y ; y -= V h1 ; (h2, ||y||^2) ; y -= V h2 ; h = h1 + h2 ;
+              // ||y_final||^2 = ||y||^2 - ||h2||^2 (V orthonormal), saving one reduction
+              const int nv = j + 1;
+              gs_vectors += nv;
+              dots_cta<S>(V, ld, nv, ycur, lo, hi, false, s);
+              PM_SUM_OR_FAIL(nv);
+              for (int k = tid; k < nv; k += nth) { s.h1[k] = s.coef[k]; hc[k] = E::coef(s.coef[k]); }
+              __syncthreads();
+              update_rows<S>(ycur, V, ld, nv, hc, lo, hi);
+              __syncthreads();
+              dots_cta<S>(V, ld, nv, ycur, lo, hi, true, s);
+              PM_SUM_OR_FAIL(nv + 1);
+              for (int k = tid; k < nv; k += nth) {
+                const double h2 = s.coef[k];
+                s.H[k * PM_MAXM + j] = s.h1[k] + h2;
+                hc[k] = E::coef(h2);
+              }
+              if (tid < 32) {   // ||h2||^2 by one warp
+                double a = 0.0;
+                for (int k = tid; k < nv; k += 32) a = fma(s.coef[k], s.coef[k], a);
+                a = pm_warp_sum(a);
+                if (tid == 0) {
+                  const double y0n = s.coef[nv];
+                  c.hn = y0n - a;                           // squared norm by Pythagoras
+                  c.measure = (a <= 0.25 * y0n) ? 0 : 1;    // not orthogonal enough: measure it
+                }
+              }
+              __syncthreads();
+              update_rows<S>(ycur, V, ld, nv, hc, lo, hi);
+              __syncthreads();
+              if (c.measure) {
+                dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
+                PM_SUM_OR_FAIL(1);
+                if (tid == 0) c.hn = s.coef[0];
+              }
+              if (tid == 0) {
+                c.hn = sqrt(fmax(c.hn, 0.0));
+                s.H[(j + 1) * PM_MAXM + j] = c.hn;
+              }
             }
+            if (tid == 0) {
+              c.kcur = j + 1;
+              if (c.hn <= c.bd_abs) {      // happy breakdown (R12): invariant subspace
+                s.H[(j + 1) * PM_MAXM + j] = 0.0;
+                c.hn = 0.0;
+                c.invariant = 1;
+              } else {
+                set_inv(c, c.hn);
+              }
+            }
+            __syncthreads();
+            if (c.invariant) break;
+          }
+          // normalise the last vector: v_{kcur} = y / ||y||  (my rows)
+          if (!c.invariant) {
+            const S* yl = Y + (size_t)((c.kcur - 1) & 1) * ld;
+            const C sc = scal_inv<S>(c);
+            for (int r = lo + tid; r < hi; r += nth) V[(size_t)c.kcur * ld + r] = E::scale(yl[r], sc);
+          }
+        }
+        // ---------------- augmented matrix (Eq. hathm + R2) and its exponential (a5)
+        // ||H_hat||_1 = max(tau ||H_m||_1, 1): the augmented columns each hold a single 1
+        if (tid < 32) {
+          const int mu = min(c.m, c.kcur);
+          double mx = 0.0;
+          for (int jj = tid; jj < mu; jj += 32) {
+            double cs = 0.0;
+            for (int i = 0; i < mu; ++i) cs += fabs(s.H[i * PM_MAXM + jj]);
+            mx = fmax(mx, c.tau_used * cs);
+          }
+          mx = pm_warp_max(mx);
+          if (tid == 0) {
+            c.m_used = mu;
+            c.hlast = (c.invariant && mu == c.kcur) ? 0.0 : s.H[mu * PM_MAXM + mu - 1];
+            c.norm1 = fmax(mx, 1.0);
+            c.sq = pm_squarings(c.norm1, prm.theta13);
+          }
+        }
+        __syncthreads();
+        const int mu = c.m_used;
+        const int ca = (p >= 1) ? mu + p - 1 : 0;
+        const int cb = mu + p;
+        if (!expm_team(team, s, prm.pade_b, c.tau_used, mu, p, c.sq, w.expm, ca, cb)) {
+          if (tid == 0) c.status = PM_ETIMEOUT;
+          goto done;
+        }
+      }
+      // ---------------- error estimate (a6) and controller (a7): thread 0
+      if (tid == 0) {
+        const int mu = c.m_used;
+        if (c.beta > 0.0) {
+          c.expms += 1;
+          c.eps = pow(c.tau_used, p + 1) * c.beta * fabs(c.hlast) * fabs(s.phi1[mu - 1]);   // Eq. (errest), R4
+        }
+        if (!isfinite(c.eps)) {
+          c.nonfinite += 1;
+          c.rejects += 1;
+          c.outcome = PM_ATT_RETRY;
+          if (c.nonfinite >= 10) { c.status = PM_ENONFINITE; c.outcome = PM_ATT_FAIL; }
+          c.tau = c.tau / 5.0;
+          ctl_reset(ctl);
+        } else {
+          c.nonfinite = 0;
+          const double eps = c.eps, tau_used = c.tau_used;
+          int m = mu;
+          const int m_max = prm.m_max;
+          const double omega = c.t_end * eps / (tau_used * c.tol);          // Eq. (taunew)
+          // Algorithm 4
+          double q;
+          bool qf;
+          if (ctl.rejected && ctl.tau_changed) {
+            q = (eps > 0.0 && ctl.eps_old > 0.0 && tau_used != ctl.tau_old)
+                    ? log(eps / ctl.eps_old) / log(tau_used / ctl.tau_old) - 1.0 : nan("");   // Eq. (6), R7
+            if (!isfinite(q)) { q = m / 4.0; qf = false; }
+            else { q = fmin(fmax(q, 0.0), (double)m); qf = true; }
+          } else if (ctl.rejected && ctl.qf) {
+            q = ctl.q; qf = true;
+          } else {
+            q = m / 4.0; qf = false;
+          }
+          ctl.q = q; ctl.qf = qf;
+          const double tau_new = (omega > 0.0) ? tau_used * pow(prm.gamma / omega, 1.0 / (q + 1.0)) : INFINITY;  // Eq. (2)
+          double kap;
+          bool kf;
+          if (ctl.rejected && ctl.m_changed) {
+            kap = (eps > 0.0 && ctl.eps_old > 0.0 && m != ctl.m_old)
+                      ? pow(eps / ctl.eps_old, 1.0 / (double)(ctl.m_old - m)) : nan("");       // Eq. (7)
+            if (!isfinite(kap) || kap <= 1.0) { kap = 2.0; kf = false; }
+            else kf = true;
+          } else if (ctl.rejected && ctl.kf) {
+            kap = ctl.kap; kf = true;
+          } else {
+            kap = 2.0; kf = false;
+          }
+          ctl.kap = kap; ctl.kf = kf;
+          const double m_new_real = (omega > 0.0) ? m + log(omega / prm.gamma) / log(kap) : -INFINITY;   // Eq. (3)
+          int m_new;
+          if (isfinite(m_new_real)) m_new = (int)fmin(fmax(ceil(m_new_real), 1.0), (double)m_max);
+          else m_new = (m_new_real < 0.0) ? 1 : m_max;
+          // cost model, Eqs. (4), (5), (8) with R13-R15
+          const double Mf = 44.0 / 3.0 + 2.0 * pm_squarings(c.norm1, prm.theta13);
+          const double t_left = c.t_end - c.t;
+          const double nnzA = (double)P.A.nnz;
+          auto C1 = [&](double mm) {
+            const double e3 = Mf * (mm + p + 1) * (mm + p + 1) * (mm + p + 1);
+            if (c.symmetric) return (mm + p) * nnzA + 3.0 * (mm + p) * n + e3;
+            return (mm + p) * nnzA + (mm * mm + 3 * p + 2) * (double)n + e3;
+          };
+          const double c_tau = ceil(t_left / tau_new) * C1((double)m);
+          const double c_m = ceil(t_left / tau_used) * C1((double)m_new);
+          bool branch_tau;
+          if (c_tau < c_m) {
+            c.tau = fmin(fmin(fmax(tau_new, tau_used / 5.0), 2.0 * tau_used), t_left);
+            branch_tau = true;
+          } else {
+            int mm = max(max(m_new, (3 * m) / 4), 1);
+            m = min(min(mm, (4 * m + 2) / 3), m_max);
+            branch_tau = false;
+          }
+          c.m = m;
+          if (omega <= prm.delta) {
+            c.outcome = PM_ATT_ACCEPT;
+            // coefficients of Eq. (step) (a8) with F of Eq. (phipapprox2)
+            const double tp = pow(tau_used, p);
+            int nvv = 0;
+            if (c.beta > 0.0) {
+              for (int i = 0; i < mu; ++i) s.ucoef[i] = tp * c.beta * s.phi0[i];
+              s.ucoef[mu] = (c.hlast != 0.0) ? tp * tau_used * c.beta * c.hlast * s.phi1[mu - 1] : 0.0;
+              nvv = (s.ucoef[mu] != 0.0) ? mu + 1 : mu;
+              for (int i = 0; i < nvv; ++i) { s.ucf[i] = (float)s.ucoef[i]; s.ucd[i] = df_from_d(s.ucoef[i]); }
+              double fn = 0.0;     // ||F|| without the corrector (FP32 guard)
+              for (int i = 0; i < mu; ++i) fn = fma(s.phi0[i], s.phi0[i], fn);
+              c.fnorm = tp * c.beta * sqrt(fn);
+            }
+            c.nvv = nvv;
             double d = 1.0;
             for (int jj = 0; jj < p; ++jj) {
               s.ucoef[PM_NSLOT + jj] = d;
               d = d * tau_used / (double)(jj + 1);
             }
+          } else {
+            c.outcome = PM_ATT_REJECT;
+            c.rejects += 1;
+            if (c.rejects > prm.max_rejects) { c.status = PM_EMAXSTEPS; c.outcome = PM_ATT_FAIL; }
+            ctl.rejected = true;
+            ctl.tau_changed = branch_tau;
+            ctl.m_changed = !branch_tau;
+            ctl.eps_old = eps;
+            ctl.tau_old = tau_used;
+            ctl.m_old = mu;
+          }
+        }
+      }
+      __syncthreads();
+      if (c.outcome == PM_ATT_FAIL) goto done;
+      if (c.outcome != PM_ATT_ACCEPT) continue;
+      {
+        // ---------------- accept: u_{k+1} = F + sum_{j<p} tau^j/j! w_j  (Eq. step)
+        // FP32 basis: F carries a relative rounding error of about u32 and cancels
+        // against the polynomial part; the candidate goes to a spare vector so that
+        // ||F|| / ||u_new|| can be bounded before it replaces u.
+        const bool guard = (E::kind == 1) && p >= 2 && c.beta > 0.0;
+        double* udst = guard ? ualt : u;
+        const int nvv = c.nvv;
+        double un = 0.0;
+        for (int r = lo + tid; r < hi; r += nth) {
+          double acc;
+          if constexpr (E::kind == 0) {
+            acc = 0.0;
+            for (int i = 0; i < nvv; ++i) acc = fma(s.ucoef[i], V[(size_t)i * ld + r], acc);
+          } else {
+            F2Acc fa = f2_zero();
+            if constexpr (E::kind == 1) {
+              for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucf[i], V[(size_t)i * ld + r]);
+            } else {
+              for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucd[i], V[(size_t)i * ld + r]);
+            }
+            acc = f2_value(fa);
+          }
+          if (p >= 1) acc = fma(s.ucoef[PM_NSLOT], u[r], acc);
+          for (int jj = 1; jj < p; ++jj) acc = fma(s.ucoef[PM_NSLOT + jj], W[(size_t)(jj - 1) * ld + r], acc);
+          udst[r] = acc;
+          if (guard) un = fma(acc, acc, un);
+        }
+        if (guard) {
+          const double v[1] = {un};
+          block_sum(s, v, 1, s.coef);
+          PM_SUM_OR_FAIL(1);
+          if (tid == 0) {
+            const double unew = sqrt(s.coef[0]);
+            c.outcome = PM_ATT_ACCEPT;
+            if (c.fnorm > PM_F32_AMP * unew && unew > 0.0) {
+              c.rejects += 1;
+              c.outcome = PM_ATT_RETRY;
+              if (c.rejects > prm.max_rejects) { c.status = PM_EMAXSTEPS; c.outcome = PM_ATT_FAIL; }
+              c.tau = c.tau_used * pow(0.5 * PM_F32_AMP * unew / c.fnorm, 1.0 / (double)(p - 1));
+              c.m = c.m_used;
+              ctl_reset(ctl);
+            }
           }
           __syncthreads();
-          // FP32 basis: F carries a relative rounding error of about u32 and cancels against
-          // sum_j tau^j/j! w_j in Eq. (step); the candidate goes to a spare vector so that
-          // ||F|| / ||u_new|| can be bounded before it replaces u.
-          const bool guard = (sizeof(S) == 4) && p >= 2 && beta > 0.0;
-          double* udst = guard ? ualt : u;
-          const int nvv = (beta > 0.0) ? ((s.ucoef[m_used] != 0.0) ? m_used + 1 : m_used) : 0;
-          double un = 0.0;
-          for (int r = lo + tid; r < hi; r += nth) {
-            double acc = 0.0;
-            for (int i = 0; i < nvv; ++i) acc = fma(s.ucoef[i], (double)V[(size_t)i * ld + r], acc);
-            if (p >= 1) acc = fma(s.ucoef[PM_NSLOT], u[r], acc);
-            for (int jj = 1; jj < p; ++jj) acc = fma(s.ucoef[PM_NSLOT + jj], W[(size_t)(jj - 1) * ld + r], acc);
-            udst[r] = acc;
-            un = fma(acc, acc, un);
-          }
-          if (guard) {
-            double v[8] = {un, 0, 0, 0, 0, 0, 0, 0};
-            block_sum8(s, v, 1, s.coef);
-            PM_SUM_OR_FAIL(1);
-            const double unew = sqrt(s.coef[0]);
-            double fn = 0.0;
-            for (int i = 0; i < m_used; ++i) fn = fma(s.phi0[i], s.phi0[i], fn);
-            fn = pow(tau_used, p) * beta * sqrt(fn);
-            if (fn > PM_F32_AMP * unew && unew > 0.0) {
-              rejects += 1;
-              if (rejects > prm.max_rejects) { status = PM_EMAXSTEPS; goto done; }
-              tau = tau_used * pow(0.5 * PM_F32_AMP * unew / fn, 1.0 / (double)(p - 1));
-              ctl.rejected = ctl.tau_changed = ctl.m_changed = ctl.qf = ctl.kf = false;
-              continue;
-            }
-            double* t2 = u; u = ualt; ualt = t2;
-          }
-          accepted = true;
-          steps += 1;
-          err_sum += eps;
-          if (steps > prm.max_steps) { status = PM_EMAXSTEPS; goto done; }
-          const bool last = tau_used >= t_end - t;
-          t = last ? t_end : t + tau_used;
-          if (t < t_end) tau = fmin(tau, t_end - t);
-          r_last_tau = tau_used;
-          r_last_m = m_used;
-          PM_SYNC_OR_FAIL();    // u complete before the next SpMV reads neighbours
-        } else {
-          rejects += 1;
-          if (rejects > prm.max_rejects) { status = PM_EMAXSTEPS; goto done; }
-          ctl.rejected = true;
-          ctl.tau_changed = branch_tau;
-          ctl.m_changed = !branch_tau;
-          ctl.eps_old = eps;
-          ctl.tau_old = tau_used;
-          ctl.m_old = m_used;
+          if (c.outcome == PM_ATT_FAIL) goto done;
+          if (c.outcome == PM_ATT_RETRY) continue;
+          double* t2 = u; u = ualt; ualt = t2;
         }
+        if (tid == 0) {
+          c.steps += 1;
+          c.err_sum += c.eps;
+          if (c.steps > prm.max_steps) c.status = PM_EMAXSTEPS;
+          const bool last = c.tau_used >= c.t_end - c.t;
+          c.t = last ? c.t_end : c.t + c.tau_used;
+          if (c.t < c.t_end) c.tau = fmin(c.tau, c.t_end - c.t);
+          c.last_tau = c.tau_used;
+          c.last_m = c.m_used;
+        }
+        PM_SYNC_OR_FAIL();    // u complete before the next SpMV reads neighbours; c visible
+        if (c.status != PM_OK) goto done;
+        break;
       }
     }
   }
@@ -908,20 +1070,21 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     for (int r = lo + tid; r < hi; r += nth) P.u[r] = u[r];
   }
 done:
+  __syncthreads();
   if (team.rank() == 0 && threadIdx.x == 0) {
-    res.status = status;
-    res.steps = steps;
-    res.rejects = rejects;
+    res.status = c.status;
+    res.steps = c.steps;
+    res.rejects = c.rejects;
     res.matvecs = matvecs;
-    res.expms = expms;
+    res.expms = c.expms;
     res.kry_steps = kry_steps;
     res.gs_vectors = gs_vectors;
-    res.err_est_sum = err_sum;
-    res.normA = r_normA;
-    res.normb = r_normb;
-    res.symmetric = symmetric ? 1 : 0;
-    res.last_tau = r_last_tau;
-    res.last_m = r_last_m;
+    res.err_est_sum = c.err_sum;
+    res.normA = c.normA;
+    res.normb = c.normb;
+    res.symmetric = c.symmetric;
+    res.last_tau = c.last_tau;
+    res.last_m = c.last_m;
   }
 #undef PM_SYNC_OR_FAIL
 #undef PM_SUM_OR_FAIL

@@ -18,7 +18,7 @@ from . import build as _build
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS = range(8)
-F64, F32_MIXED = 0, 1
+F64, F32_MIXED, F64_PAIR = 0, 1, 2
 OP_CSR, OP_STENCIL = 0, 1
 M_MAX, P_MAX = 64, 8
 
@@ -169,13 +169,14 @@ def _stream_ptr(stream):
 class Phipm:
     """A library handle: owns the device workspace.
 
-    precision: "f64" (PHIPM_F64) or "f32" (PHIPM_F32_MIXED); other keyword
-    arguments override phipm_params fields (gamma, delta, m_init, m_max, ...)."""
+    precision: "f64" (PHIPM_F64, IEEE FP64), "f64pair" (PHIPM_F64_PAIR, FP64-class
+    accuracy from float pairs on the FP32 pipe) or "f32" (PHIPM_F32_MIXED); other
+    keyword arguments override phipm_params fields (gamma, delta, m_init, ...)."""
 
     def __init__(self, precision: str = "f64", **overrides):
         L = lib()
         self.params = default_params()
-        self.params.precision = F32_MIXED if precision == "f32" else F64
+        self.params.precision = {"f64": F64, "f32": F32_MIXED, "f64pair": F64_PAIR}[precision]
         for k, v in overrides.items():
             setattr(self.params, k, v)
         h = c_void_p()
