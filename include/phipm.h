@@ -43,7 +43,8 @@ typedef enum {
   PHIPM_ENONFINITE = 4,   /* ten non-finite error estimates in a row               */
   PHIPM_EMAXSTEPS = 5,    /* params.max_steps or params.max_rejects exceeded       */
   PHIPM_ETIMEOUT = 6,     /* a bounded device-side wait gave up                    */
-  PHIPM_EBOUNDS = 7       /* a device-side bounds check failed                     */
+  PHIPM_EBOUNDS = 7,      /* a device-side bounds check failed                     */
+  PHIPM_ETOOLARGE = 8     /* problem larger than phipm_solve_noalloc's static scratch */
 } phipm_status;
 
 typedef enum {
@@ -167,6 +168,32 @@ phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, const double* t
                                  const double* const* const* b, const double* tol,
                                  const int32_t* symm, double* const* u, phipm_stats* stats,
                                  phipm_status* per_problem, void* stream);
+
+/* Allocation-free solve (the paper has no counterpart; this is a library service).
+ *
+ * For callers that must not allocate device memory: for example a plugin whose
+ * host application reserves all device memory up front and refuses further
+ * cudaMalloc calls, or a latency-bound loop that cannot afford cudaMalloc's
+ * implicit device synchronisation.  phipm_create allocates (its workspace, its
+ * events), so this entry point needs no handle and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its workspace is one file-scope
+ * __device__ array of about 5.5 MB that every GPU which loads the library holds
+ * until the process exits.
+ *
+ * Same arguments and result as phipm_solve with the default parameters
+ * (PHIPM_F64, one CTA per solve), device buffers, except that n must be at most
+ * PHIPM_NOALLOC_MAX_N and p at most PHIPM_P_MAX; larger problems return
+ * PHIPM_ETOOLARGE before any GPU work.  stats->kernel_ms is 0.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's contents (the kernel clears what must start at zero): calls whose work
+ * overlaps on the GPU, e.g. on two streams at once, race on it and must be
+ * serialised by the caller.  The call synchronises the stream before returning. */
+#define PHIPM_NOALLOC_MAX_N 8192
+phipm_status phipm_solve_noalloc(double t_end, const phipm_operator* A, int32_t p, const double* const* b,
+                                 double tol, int32_t symm, double* u, phipm_stats* stats, void* stream);
 
 #ifdef __cplusplus
 }

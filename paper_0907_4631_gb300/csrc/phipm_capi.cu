@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -682,4 +683,97 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   }
   if (overall != PHIPM_OK) return fail(h, overall, status_text(overall));
   return PHIPM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// allocation-free solve: the workspace of one single-CTA FP64 solve lives in a
+// file-scope device array (n <= PHIPM_NOALLOC_MAX_N)
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr long long kNaLd = PHIPM_NOALLOC_MAX_N;                        // multiple of 64
+constexpr long long kNaV = 0;                                           // (m_max+1) basis vectors
+constexpr long long kNaW = kNaV + (PM_MAXM + 1) * kNaLd * 8;            // w_1..w_p + spare
+constexpr long long kNaY = kNaW + (PM_MAXP + 1) * kNaLd * 8;            // two Krylov vectors
+constexpr long long kNaE = (kNaY + 2 * kNaLd * 8 + 255) & ~255ll;       // exponential scratch
+constexpr long long kNaR = (kNaE + (long long)PM_EXPM_DOUBLES * 8 + 255) & ~255ll;   // result record
+constexpr long long kNaBytes = (kNaR + (long long)sizeof(DevResult) + 255) & ~255ll;
+}  // namespace
+
+// Only the host-side address lookup below may name this array from host code:
+// on the host its name is a stand-in, not a device address.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+__global__ void __launch_bounds__(PM_THREADS, 1)
+k_solve_noalloc(DevProblem P, DevParams prm, unsigned char* scratch) {
+  extern __shared__ __align__(16) unsigned char pm_smem[];
+  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
+  DevResult* res = reinterpret_cast<DevResult*>(scratch + kNaR);
+  if (threadIdx.x == 0) memset(res, 0, sizeof(DevResult));   // the array keeps the last call's contents
+  __syncthreads();
+  P.V = scratch + kNaV;
+  P.W = reinterpret_cast<double*>(scratch + kNaW);
+  P.Y = scratch + kNaY;
+  P.ld = kNaLd;
+  PmWork w{nullptr, reinterpret_cast<double*>(scratch + kNaE)};
+  CtaTeam team;
+  phipm_device<CtaTeam, double>(team, P, prm, *res, s, w);
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNaMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" phipm_status phipm_solve_noalloc(double t_end, const phipm_operator* A, int32_t p,
+                                           const double* const* b, double tol, int32_t symm, double* u,
+                                           phipm_stats* stats, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  long long nnz_model = 0;
+  if (check_operator(nullptr, A, nnz_model) != PHIPM_OK) return PHIPM_EINVAL;
+  if (!(t_end > 0) || !std::isfinite(t_end) || !std::isfinite(tol) || symm < -1 || symm > 1 || p < 0)
+    return PHIPM_EINVAL;
+  const int n = op_n(A);
+  if (n > PHIPM_NOALLOC_MAX_N || p > PHIPM_P_MAX) return PHIPM_ETOOLARGE;
+  if (n > 0 && (!b || !u)) return PHIPM_EINVAL;
+  for (int k = 0; k <= p && n > 0; ++k)
+    if (!b[k]) return PHIPM_EINVAL;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (n == 0) return PHIPM_OK;
+  // once per device, with that device current: the array's device address
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return PHIPM_ECUDA;
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return PHIPM_ECUDA;
+      if (cudaFuncSetAttribute(k_solve_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PmShared)) !=
+          cudaSuccess)
+        return PHIPM_ECUDA;
+      g_noalloc_ptr[dev] = (unsigned char*)ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  phipm_params defaults;
+  phipm_default_params(&defaults);
+  DevProblem P;
+  memset(&P, 0, sizeof(P));
+  P.A = make_devop(A, nnz_model);
+  P.p = p;
+  P.symm = symm;
+  P.t_end = t_end;
+  P.tol = tol;
+  for (int k = 0; k <= p; ++k) P.b[k] = b[k];
+  P.u = u;
+  const DevParams prm = make_params(defaults);
+  k_solve_noalloc<<<1, PM_THREADS, sizeof(PmShared), stream>>>(P, prm, scratch);
+  if (cudaGetLastError() != cudaSuccess) return PHIPM_ECUDA;
+  DevResult r;
+  if (cudaMemcpyAsync(&r, scratch + kNaR, sizeof(DevResult), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    return PHIPM_ECUDA;
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return PHIPM_ECUDA;
+  if (stats) fill_stats(stats, r, 0.f);
+  return map_status(r.status);
 }

@@ -17,10 +17,10 @@ from . import build as _build
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE = range(9)
 F64, F32_MIXED, F64_PAIR = 0, 1, 2
 OP_CSR, OP_STENCIL = 0, 1
-M_MAX, P_MAX = 64, 8
+M_MAX, P_MAX, NOALLOC_MAX_N = 64, 8, 8192
 
 
 class CsrC(ctypes.Structure):
@@ -89,6 +89,9 @@ def lib(build_if_needed: bool = True):
                                       ctypes.POINTER(c_double), ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p),
                                       ctypes.POINTER(StatsC), ctypes.POINTER(c_int32), c_void_p]
     L.phipm_solve_batched.restype = c_int32
+    L.phipm_solve_noalloc.argtypes = [c_double, ctypes.POINTER(OperatorC), c_int32, ctypes.POINTER(c_void_p),
+                                      c_double, c_int32, c_void_p, ctypes.POINTER(StatsC), c_void_p]
+    L.phipm_solve_noalloc.restype = c_int32
     _LIB = L
     return L
 
@@ -258,3 +261,18 @@ class Phipm:
         if check:
             self._check(st)
         return outs, [s.as_dict() for s in ST], list(PS)
+
+
+def solve_noalloc(t_end: float, A: DeviceOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,
+                  stream=None):
+    """phipm_solve_noalloc: the FP64 solve with the library's static device scratch
+    (no handle, no device allocation inside the call).  Returns (u, stats, status)."""
+    import torch
+    n = A.n
+    p = len(b) - 1
+    u = out if out is not None else torch.empty(n, dtype=torch.float64, device=b[0].device)
+    bp = (c_void_p * (p + 1))(*[x.data_ptr() for x in b])
+    stats = StatsC()
+    st = lib().phipm_solve_noalloc(float(t_end), ctypes.byref(A.c), p, bp, float(tol), int(symm),
+                                   c_void_p(u.data_ptr()), ctypes.byref(stats), _stream_ptr(stream))
+    return u, stats.as_dict(), st

@@ -1,0 +1,49 @@
+"""phipm_solve_noalloc: the solve for callers that must not allocate device memory.
+
+Some callers cannot call cudaMalloc (a host application that owns all device
+memory, a latency-bound loop that cannot afford cudaMalloc's implicit
+synchronisation).  This entry point runs the single-CTA FP64 solve with its
+workspace in a static device array of the library.  This file is collected
+last, so a run that stops at the first failure has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_0907_4631_gb300 import phipm as pm
+from paper_0907_4631_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-8
+
+
+def _dev(b):
+    return [torch.as_tensor(np.ascontiguousarray(x)).cuda() for x in b]
+
+
+def test_noalloc_matches_phipm_solve_on_two_calls():
+    pr = wl.convdiff_2d_problem(N=64, p=3, t_end=1e-3, tol=1e-8, seed=2964)   # n = 4096 <= 8192
+    A = pm.DeviceOperator(pr.op)
+    b = _dev(pr.b)
+    ref, ref_stats, st = pm.Phipm("f64").solve(pr.t_end, A, b, pr.tol, 0)
+    assert st == pm.OK
+    ref = ref.cpu().numpy()
+    for _ in range(2):                       # the static array keeps the previous call's contents
+        u, stats, st = pm.solve_noalloc(pr.t_end, A, b, pr.tol, 0)
+        torch.cuda.synchronize()
+        assert st == pm.OK
+        u = u.cpu().numpy()
+        assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= TOL64
+        assert stats["steps"] == ref_stats["steps"] and stats["rejects"] == ref_stats["rejects"]
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    st = wl.laplacian(2, 91)                 # n = 8281 > 8192
+    A = pm.DeviceOperator(st)
+    b = _dev([np.ones(st.n)])
+    _, _, status = pm.solve_noalloc(1e-3, A, b, 1e-8, 1)
+    assert status == pm.ETOOLARGE
