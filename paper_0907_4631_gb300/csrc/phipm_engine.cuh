@@ -806,7 +806,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               }
             } else {
               // CGS2: h1 = V^T y ; y -= V h1 ; (h2, ||y||^2) ; y -= V h2 ; h = h1 + h2 ;
-              // ||y_final||^2 = ||y||^2 - ||h2||^2 (V orthonormal), saving one reduction
+              // ||y_final||^2 = ||y||^2 - ||h2||^2 (V orthonormal) replaces the last
+              // reduction by a plain team barrier
               const int nv = j + 1;
               gs_vectors += nv;
               dots_cta<S>(V, ld, nv, ycur, lo, hi, false, s);
@@ -839,6 +840,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
                 dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
                 PM_SUM_OR_FAIL(1);
                 if (tid == 0) c.hn = s.coef[0];
+              } else {
+                // the next SpMV reads other CTAs' rows of y: they must have finished this update
+                PM_SYNC_OR_FAIL();
               }
               if (tid == 0) {
                 c.hn = sqrt(fmax(c.hn, 0.0));
