@@ -49,6 +49,11 @@ Readings where the paper is silent, garbled or contradicts itself
       drives the scaling of the exponential.
   R15 the cost model follows the symmetry of A (Lanczos or Arnoldi formula of
       Eq. 4), whatever orthogonalisation an implementation uses.
+  R19 the m branch is only taken when it changes m: if m_new, restricted to a
+      factor 4/3 and to [1, m_max], equals the current m (m at m_max with the
+      tolerance still missed, say), tau changes instead.  Sec. 3.4 does not
+      say what happens at the bound; taken literally the rejected attempt
+      would repeat unchanged for ever.
 """
 from __future__ import annotations
 
@@ -436,17 +441,19 @@ def phipm(t_end: float, A, b, tol: float = 1e-7, symm: int = -1, params: dict | 
             t_left = t_end - t
             c_tau = total_cost(tau_new, m, t_left, p, nnz, n, M, symmetric)
             c_m = total_cost(tau_used, m_new, t_left, p, nnz, n, M, symmetric)
-            if c_tau < c_m:                                            # Algorithm 3 branch
+            m_cand = min(max(m_new, (3 * m) // 4, 1), math.ceil(4 * m / 3), m_max)
+            if c_tau < c_m or m_cand == m:              # Algorithm 3 branch; reading R19 at the m bounds
                 tau = min(max(tau_new, tau_used / 5.0), 2.0 * tau_used, t_left)
                 branch = "tau"
             else:
-                m = min(max(m_new, (3 * m) // 4, 1), math.ceil(4 * m / 3), m_max)
+                m = m_cand
                 branch = "m"
             accepted = omega <= prm["delta"]
             if trace is not None:
                 trace.append(dict(step=stats.steps, t=t, tau=tau_used, m=m_eff, eps=eps, omega=omega,
                                   accepted=accepted, q_hat=q, kappa_hat=kap, tau_new=tau_new,
-                                  m_new=m_new, branch=branch, beta=beta, next_tau=tau, next_m=m))
+                                  m_new=m_new, branch=branch, beta=beta, next_tau=tau, next_m=m,
+                                  cost_tau=c_tau, cost_m=c_m))
             if accepted:
                 break
             stats.rejects += 1

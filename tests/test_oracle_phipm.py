@@ -226,3 +226,24 @@ def test_long_horizon_error_budget():
     assert st.steps >= 3
     assert st.err_est_sum <= 1.2 * tol * (1 + 1e-12)
     assert np.linalg.norm(u - T.solution_diagonal(lam, b, 50.0)) <= 3 * tol
+
+
+def test_m_branch_at_m_max_changes_tau():
+    """Reading R19: at m = m_max with the tolerance missed, the cost comparison can favour the
+    m branch although m cannot grow; tau must change instead, and the result stays accurate
+    (dense augmented exponential).  A strongly convective problem with m_max = 24 meets it."""
+    st = wl.convection_diffusion_2d(16, 1.0, 800.0, 240.0)
+    op = wl.stencil_to_csr(st)
+    b = [wl.normal(11, k, st.n) for k in range(2)]
+    trace = []
+    u, stats = O.phipm(4e-3, op, b, 1e-8, 0, params=dict(m_max=24), trace=trace)
+    blocked = [r for r in trace if r["m"] == 24 and not r["accepted"] and r["cost_m"] <= r["cost_tau"]]
+    assert blocked, "the case no longer reaches the m bound"
+    for r in blocked:
+        assert r["branch"] == "tau" and r["next_tau"] < r["tau"]
+    # consecutive attempts never repeat the same (tau, m)
+    for a, c in zip(trace, trace[1:]):
+        if not a["accepted"]:
+            assert (a["tau"], a["m"]) != (c["tau"], c["m"])
+    ut = T.solution_dense_augmented(wl.csr_to_dense(op), b, 4e-3)
+    assert np.linalg.norm(u - ut) <= 2e-8
