@@ -38,11 +38,39 @@ WORKLOADS = {
                            precision="f64pair"),
     "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64pair"),
     "laplacian3d_128": dict(metric_cfg="FP32-basis 128^3 Laplacian stencil, p=2, tol 1e-5", precision="f32"),
+    "batched_convdiff_256": dict(metric_cfg="256 independent convection-diffusion problems, sides U{64..256}, "
+                                            "p U{1..4}, tol 1e-8, one persistent launch replayed as a CUDA graph",
+                                 precision="f64pair", batched=True),
+    "batched_convdiff_256_f32": dict(metric_cfg="the same 256 problems with an FP32 Krylov basis, tol 1e-5",
+                                     precision="f32", batched=True, tol=1e-5),
+    "peclet_128_1024_learned": dict(metric_cfg="1024 held-out convection-diffusion 128x128 problems, Peclet "
+                                               "log-uniform [1,1e3], tol 1e-8, learned (tau, m) controller",
+                                    precision="f64pair", batched=True, learned=True),
 }
 DTYPES = {"f64": "f64", "f32": "f32 basis (FP64 coefficients, H, expm, eps, u)",
           "f64pair": "f32x2 float pairs on the FP32 pipe (FP64-class; FP64 w-recurrence, H, expm, eps, u)"}
 METRIC = "solves/s at rel.err<=1e-8 vs FP64 oracle; SpMV+Arnoldi HBM GB/s vs peak"
 PEAK_FALLBACK = 6800.0
+
+
+def make_batch(name: str, first: int = 0, count: int | None = None) -> list:
+    """Problems [first, first+count) of a batched workload (each depends on its own seed only)."""
+    from paper_0907_4631_gb300 import workloads as wl
+    spec = WORKLOADS[name]
+    if name.startswith("batched_convdiff_256"):
+        total = 256
+        cnt = total - first if count is None else count
+        probs = wl.batched_convdiff_problems(count=cnt, seed0=4000 + first)
+    elif name == "peclet_128_1024_learned":
+        total = 1024
+        cnt = total - first if count is None else count
+        probs = wl.peclet_convdiff_problems(count=cnt, seed0=5000 + first)
+    else:
+        raise ValueError(name)
+    if "tol" in spec:
+        for pr in probs:
+            pr.tol = spec["tol"]
+    return probs
 
 
 def make_problem(name: str):
@@ -156,6 +184,45 @@ print(json.dumps(dict(seconds=dt, steps=st.steps, rejects=st.rejects)))
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def _oracle_batch_worker(job):
+    """One oracle solve of problem idx of a batched workload (in a spawned process)."""
+    import time as _t
+    import numpy as _np
+    from oracle import phipm_oracle as O
+    workload, idx, path = job
+    pr = make_batch(workload, idx, 1)[0]
+    t0 = _t.perf_counter()
+    u, st = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, pr.symm)
+    dt = _t.perf_counter() - t0
+    _np.save(path, u)
+    return dt, st.steps, st.rejects
+
+
+def run_oracle_pool(workload: str, indices: list, tmpdir: str) -> tuple:
+    """Oracle solves of the given problems, spread over the host cores by a spawned
+    process pool (single-threaded BLAS each).  Returns (wall seconds, cores, per-problem u paths)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    cores = max(1, min(len(indices), os.cpu_count() or 1))
+    paths = [os.path.join(tmpdir, f"u_{i}.npy") for i in indices]
+    ctx = mp.get_context("spawn")
+    saved = os.environ.get("CUDA_VISIBLE_DEVICES")
+    os.environ["CUDA_VISIBLE_DEVICES"] = ""
+    try:
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_batch_worker, [(workload, 0, os.path.join(tmpdir, "warm.npy"))] * cores, chunksize=1)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_batch_worker, [(workload, i, pth) for i, pth in zip(indices, paths)], chunksize=1)
+            wall = time.perf_counter() - t0
+    finally:
+        if saved is None:
+            del os.environ["CUDA_VISIBLE_DEVICES"]
+        else:
+            os.environ["CUDA_VISIBLE_DEVICES"] = saved
+    return wall, cores, paths, res
+
+
 def traffic_from_profiles(kernel: str, workload: str):
     """dram bytes per launch from a committed ncu summary, if it matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -170,8 +237,40 @@ def traffic_from_profiles(kernel: str, workload: str):
         return None
 
 
+def reference_arm_batched(args, world):
+    """The oracle on bounded samples of a batched workload: each step solves one problem
+    per host core (a window moving through the batch), spread over spawned processes."""
+    count = len(make_batch(args.workload))
+    cores = os.cpu_count() or 1
+    secs, solved = [], 0
+    with tempfile.TemporaryDirectory() as td:
+        for k in range(args.warmup + args.steps):
+            idx = [((k * cores + j) * 7) % count for j in range(cores)]
+            wall, used, _, _ = run_oracle_pool(args.workload, idx, td)
+            if k >= args.warmup:
+                secs.append(wall)
+                solved += len(idx)
+    total = sum(secs)
+    value = solved / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded counter-based generator)",
+        "config": {"workload": args.workload, "problems": count},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": min(cores, count), "kind": "oracle",
+                         "sample": f"per step {cores} problems of the batch, one FP64 oracle solve each over "
+                                   f"spawned processes (value = problems / seconds)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
+        return
+    if WORKLOADS[args.workload].get("batched"):
+        reference_arm_batched(args, world)
         return
     pr = make_problem(args.workload)
     # each step: the oracle over a fraction f of [0, t_end], so the run stays within minutes
@@ -197,6 +296,247 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_batch(batch, stream, flush, steps, packed=None):
+    """Event-timed repeats of one batched solve; with packed, each repeat also uploads the
+    inputs from pinned host memory and downloads every u (the end-to-end leg)."""
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if packed is not None:
+            packed.upload(stream)
+        batch.run(stream)
+        if packed is not None:
+            packed.download(stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def run_batched(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_0907_4631_gb300 import phipm as pm
+    spec = WORKLOADS[args.workload]
+    prec = spec["precision"]
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    probs = make_batch(args.workload)
+    count = len(probs)
+    solver = pm.Phipm(prec)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    learned = None
+    if spec.get("learned"):
+        from paper_0907_4631_gb300 import learned as L
+        t0 = time.perf_counter()
+        tr = L.training_problems(count=384, seed0=7000)
+        X, T = L.examples_from_traces(L.collect_traces(solver, tr))
+        blob, losses = L.train(solver, X, T, iters=3000, lr=3e-3)
+        solver.set_controller_weights(blob)
+        learned = {"training_problems": len(tr), "examples": int(X.shape[0]), "adam_iters": 3000,
+                   "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                   "train_seconds": time.perf_counter() - t0}
+    pk = PackedBatch(probs)
+    batch = solver.batch([pr.t_end for pr in probs], pk.ops, pk.bs, [pr.tol for pr in probs],
+                         [pr.symm for pr in probs], outs=pk.outs)
+
+    def measure(controller):
+        solver.set_controller(controller)
+        for _ in range(args.warmup):
+            batch.run(stream)
+        torch.cuda.synchronize()
+        return time_batch(batch, stream, flush, args.steps), batch.stats()
+
+    plain = None
+    if learned is not None:
+        pt, pst = measure(0)
+        plain = {"value": world * count * args.steps / (sum(pt) / 1e3), "unit": "solves/s",
+                 "rejects": int(sum(x["rejects"] for x in pst)), "steps": int(sum(x["steps"] for x in pst)),
+                 "matvecs": int(sum(x["matvecs"] for x in pst)),
+                 "krylov_steps": int(sum(x["krylov_steps"] for x in pst))}
+        u_plain = [u.cpu().numpy() for u in pk.outs]
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        batch.run(stream)
+    solver.set_controller(1 if learned is not None else 0)
+    for _ in range(args.warmup):
+        batch.run(stream)
+    torch.cuda.synchronize()
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = time_batch(batch, stream, flush, args.steps)
+    stats = batch.stats()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * count * args.steps / (total_ms / 1e3)
+    kernel_ms = stats[0]["kernel_ms"]
+    u_gpu = [u.cpu().numpy() for u in pk.outs]
+
+    # end to end: inputs uploaded from one pinned host buffer, every u downloaded, each step
+    e2e = None
+    if not args.no_e2e:
+        et = time_batch(batch, stream, flush, args.steps, packed=pk)
+        tot = sum(et)
+        if dist:
+            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": world * count * args.steps / (tot / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": int(pk.in_bytes), "d2h_bytes_per_step": int(pk.out_bytes)}
+
+    # the plain FP64 GPU solver, one problem per call, on an evenly spaced sample
+    sample = list(range(0, count, max(1, count // 32)))
+    f64 = pm.Phipm("f64")
+    for i in sample[:3]:
+        f64.solve(probs[i].t_end, pk.ops[i], pk.bs[i], probs[i].tol, probs[i].symm)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in sample:
+        f64.solve(probs[i].t_end, pk.ops[i], pk.bs[i], probs[i].tol, probs[i].symm)
+    e1.record(stream)
+    e1.synchronize()
+    plain_f64 = {"value": len(sample) / (e0.elapsed_time(e1) / 1e3), "unit": "solves/s",
+                 "sample": f"{len(sample)} problems (every {max(1, count // 32)}th), one phipm_solve each, "
+                           f"FP64 basis, same tol"}
+
+    peak, peak_kind = measured_peaks()
+    abytes = sum(algorithmic_bytes(pr, st, prec) for pr, st in zip(probs, stats))
+    achieved = abytes / (kernel_ms / 1e3) / 1e9
+    traffic = traffic_from_profiles("k_solve_queue", args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_solve_queue",
+                "algorithmic_bytes_per_launch": abytes, "kernel_ms": kernel_ms}
+    sizes = [pr.n for pr in probs]
+    convert = prec != "f64"
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
+        "data": "synthetic (seeded counter-based generator; same inputs as the oracle)",
+        "config": {"workload": args.workload, "problems": count, "n_min": min(sizes), "n_max": max(sizes),
+                   "n_total": int(sum(sizes)), "tol": probs[0].tol,
+                   "l2": "flushed between timed batches (256 MiB write)",
+                   "launch": "one persistent queue kernel per batch, replayed from a captured CUDA graph",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "solver_stats": {k: int(sum(x[k] for x in stats)) for k in ("steps", "rejects", "matvecs", "expms",
+                                                                     "krylov_steps", "gs_vectors")},
+        "gpu_launches": args.steps * (2 if convert else 1),
+        "roofline": roofline,
+        "clocks": clocks,
+        "plain_fp64_gpu_solver": plain_f64,
+    }
+    if learned is not None:
+        line["learned"] = learned
+        line["plain_controller"] = plain
+        line["plain_vs_learned_max_rel_diff"] = float(max(
+            np.linalg.norm(a - b_) / np.linalg.norm(b_) for a, b_ in zip(u_gpu, u_plain)))
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        csample = list(range(0, count, max(1, count // 48)))[:48]
+        with tempfile.TemporaryDirectory() as td:
+            wall, cores, paths, res = run_oracle_pool(args.workload, csample, td)
+            errs = []
+            for i, pth in zip(csample, paths):
+                ur = np.load(pth)
+                errs.append(float(np.linalg.norm(u_gpu[i] - ur) / np.linalg.norm(ur)))
+        line["cpu_baseline"] = {"value": len(csample) / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{len(csample)} of the {count} problems (evenly spaced), one FP64 "
+                                          f"oracle solve each, spread over {cores} spawned processes"}
+        line["rel_err_vs_oracle"] = {"max": max(errs), "median": statistics.median(errs), "problems": len(errs)}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+class PackedBatch:
+    """All inputs of a batch in one pinned host buffer and one device buffer (256-byte
+    aligned arrays), so the end-to-end leg moves them with one copy each way."""
+
+    def __init__(self, probs):
+        import numpy as np
+        import torch
+        from paper_0907_4631_gb300 import phipm as pm
+        lay, off = [], 0
+
+        def take(nbytes):
+            nonlocal off
+            o = off
+            off += (nbytes + 255) // 256 * 256
+            return o
+        for pr in probs:
+            ent = {"b": [take(8 * pr.n) for _ in pr.b]}
+            if hasattr(pr.op, "rowptr"):
+                ent["csr"] = (take(4 * (pr.n + 1)), take(4 * pr.op.nnz), take(8 * pr.op.nnz))
+            lay.append(ent)
+        in_bytes = off
+        self.u_off = [take(8 * pr.n) for pr in probs]
+        self.in_bytes, self.out_bytes = in_bytes, off - in_bytes
+        host = np.zeros(off, dtype=np.uint8)
+        for pr, ent in zip(probs, lay):
+            for o, x in zip(ent["b"], pr.b):
+                host[o:o + 8 * pr.n] = np.ascontiguousarray(x, dtype=np.float64).view(np.uint8)
+            if "csr" in ent:
+                for o, x, dt in zip(ent["csr"], (pr.op.rowptr, pr.op.colind, pr.op.values),
+                                    (np.int32, np.int32, np.float64)):
+                    a = np.ascontiguousarray(x, dtype=dt).view(np.uint8)
+                    host[o:o + a.size] = a
+        self.host = torch.from_numpy(host).pin_memory()
+        self.dev = torch.empty(off, dtype=torch.uint8, device="cuda")
+        self.dev.copy_(self.host)
+
+        def view(o, count, dt):
+            return self.dev[o:o + count * torch.empty((), dtype=dt).element_size()].view(dt)
+        self.ops, self.bs = [], []
+        for pr, ent in zip(probs, lay):
+            self.bs.append([view(o, pr.n, torch.float64) for o in ent["b"]])
+            arrays = None
+            if "csr" in ent:
+                arrays = (view(ent["csr"][0], pr.n + 1, torch.int32), view(ent["csr"][1], pr.op.nnz, torch.int32),
+                          view(ent["csr"][2], pr.op.nnz, torch.float64))
+            self.ops.append(pm.DeviceOperator(pr.op, arrays=arrays))
+        self.outs = [view(o, pr.n, torch.float64) for o, pr in zip(self.u_off, probs)]
+        self.host_out = torch.empty(self.out_bytes, dtype=torch.uint8).pin_memory()
+
+    def upload(self, stream):
+        with torch_stream(stream):
+            self.dev[:self.in_bytes].copy_(self.host[:self.in_bytes], non_blocking=True)
+
+    def download(self, stream):
+        with torch_stream(stream):
+            self.host_out.copy_(self.dev[self.in_bytes:], non_blocking=True)
+
+    def u_host(self, i, n):
+        o = self.u_off[i] - self.in_bytes
+        return self.host_out[o:o + 8 * n].numpy().view("<f8")
+
+
+def torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,6 +555,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         reference_arm(args, world, rank)
+        return
+    if WORKLOADS[args.workload].get("batched"):
+        run_batched(args, world, rank, local)
         return
 
     import numpy as np
@@ -321,7 +664,7 @@ def main():
                    "p": pr.p, "t_end": pr.t_end, "tol": pr.tol, "l2": "flushed between timed solves (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "solver_stats": {k: stats[k] for k in ("steps", "rejects", "matvecs", "expms", "krylov_steps", "gs_vectors")},
-        "gpu_launches": args.steps * (2 if (spec["precision"] == "f32" and hasattr(pr.op, "rowptr")) else 1),
+        "gpu_launches": args.steps * (2 if (spec["precision"] != "f64" and hasattr(pr.op, "rowptr")) else 1),
         "roofline": roofline,
         "clocks": clocks,
     }

@@ -169,6 +169,71 @@ phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, const double* t
                                  const int32_t* symm, double* const* u, phipm_stats* stats,
                                  phipm_status* per_problem, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Attempt traces (the records behind the paper's Figs. 2-3, Sec. 4.1: t, tau,
+ * m, the estimate and accept/reject of every attempt), and the learned (tau, m)
+ * controller trained on them.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t problem;    /* index of the problem in the call (0 for single solves)          */
+  int32_t step;       /* accepted steps before this attempt                              */
+  int32_t attempt;    /* attempt number within the step, from 0                          */
+  int32_t accepted;   /* 1 if omega <= delta                                             */
+  int32_t m_req;      /* Krylov dimension requested for the attempt                      */
+  int32_t m_used;     /* dimension used (smaller after a happy breakdown)                */
+  int32_t p;          /* number of phi terms minus one                                   */
+  int32_t n;          /* problem size                                                    */
+  double t;           /* start of the step                                               */
+  double t_end;
+  double tau;         /* step size of the attempt                                        */
+  double eps;         /* error estimate, Eq. (errest) with the tau^{p+1} scaling         */
+  double omega;       /* t_end eps / (tau Tol), Eq. (taunew)                             */
+  double norm_a;      /* ||A||_inf                                                       */
+  double tol;
+  int32_t source;     /* 0: tau, m from Algorithms 3-4; 1: proposed by the learned controller */
+  int32_t rejects_prev; /* rejected attempts in the previous step                        */
+} phipm_trace_record;
+
+/* Record up to capacity attempts of every later solve call (0 disables).  The
+ * buffer restarts at each call.  phipm_trace_read copies up to max records of the
+ * last call to host memory and sets *count to the number the call produced
+ * (records beyond capacity are dropped). */
+phipm_status phipm_trace_enable(phipm_handle* h, int64_t capacity);
+phipm_status phipm_trace_read(phipm_handle* h, phipm_trace_record* out, int64_t max, int64_t* count);
+
+/* The controller network: 8 inputs, two hidden layers of 64 GELU units, 2
+ * outputs, FP32; PHIPM_MLP_PARAMS weights laid out as W1[64x8], b1[64],
+ * W2[64x64], b2[64], W3[2x64], b3[2] (row-major).  A controller blob appends
+ * x_mean[8], x_std[8], y_mean[2], y_std[2].
+ *
+ * Inputs (before normalisation), at the start of each step:
+ *   log10(||A||_inf t_end), log10(Tol), p, log10(tau_start ||A||_inf),
+ *   m_start / 64, log10(omega of the previous accepted attempt), rejected
+ *   attempts in the previous step, log10(n),
+ * where tau_start, m_start are the values Algorithm 3 carries into the step.
+ * Outputs: log2(tau / tau_start) and m / 64 of the proposal.  With
+ * params.controller = 1 and a blob installed, the first attempt of each of the
+ * first 48 steps of a solve uses the proposal (tau ratio clamped to [1/32, 8] and
+ * to the remaining interval, m to [1, m_max]); the error estimate still accepts
+ * or rejects it, after a rejection the paper's controller takes over for the rest
+ * of the step, and from step 48 on it runs alone (so a poor network costs a
+ * bounded number of steps). */
+#define PHIPM_MLP_PARAMS 4866
+#define PHIPM_CONTROLLER_FLOATS (PHIPM_MLP_PARAMS + 20)
+phipm_status phipm_set_controller_weights(phipm_handle* h, const float* blob, size_t count);
+
+/* Device pointers; X is [n x 8], T and Y are [n x 2], row-major FP32.
+ * phipm_mlp_forward: Y = f(X) with weights w (PHIPM_MLP_PARAMS, no normalisation).
+ * phipm_mlp_grad: grad = d/dw mean((f(X) - T)^2) over all n*2 entries, and *loss.
+ * phipm_mlp_train: `iters` full-batch Adam steps on w with moments m, v (device,
+ * PHIPM_MLP_PARAMS each), step counter starting at t0+1; losses (host, may be NULL)
+ * receives the loss before each step. */
+phipm_status phipm_mlp_forward(phipm_handle* h, const float* w, const float* X, int64_t n, float* Y, void* stream);
+phipm_status phipm_mlp_grad(phipm_handle* h, const float* w, const float* X, const float* T, int64_t n,
+                            float* grad, float* loss, void* stream);
+phipm_status phipm_mlp_train(phipm_handle* h, float* w, float* m, float* v, const float* X, const float* T,
+                             int64_t n, int32_t iters, int64_t t0, float lr, float* losses, void* stream);
+
 /* Allocation-free solve (the paper has no counterpart; this is a library service).
  *
  * For callers that must not allocate device memory: for example a plugin whose

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libphipm.so")
 SOURCES = ["phipm_capi.cu"]
-HEADERS = ["phipm_common.cuh", "phipm_elem.cuh", "phipm_engine.cuh"]
+HEADERS = ["phipm_common.cuh", "phipm_elem.cuh", "phipm_engine.cuh", "phipm_mlp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

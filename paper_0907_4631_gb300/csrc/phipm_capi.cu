@@ -65,15 +65,15 @@ k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams pr
   }
 }
 
-// CSR values converted for the FP32 basis (valf) or the float-pair basis (val2),
-// one CTA per problem.
+// CSR values converted for the FP32 basis (valf) or the float-pair basis (val2);
+// blockIdx.y selects the problem, blockIdx.x strides over its values.
 __global__ void k_convert_values(const DevProblem* probs, int count, int mode) {
-  const int id = blockIdx.x;
+  const int id = blockIdx.y;
   if (id >= count) return;
   const DevOp& A = probs[id].A;
   if (A.kind != 0) return;
   const long long nnz = A.nnz;
-  for (long long k = threadIdx.x; k < nnz; k += blockDim.x) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += (long long)gridDim.x * blockDim.x) {
     const double v = A.val[k];
     if (mode == 1) {
       ((float*)A.valf)[k] = (float)v;
@@ -132,6 +132,17 @@ struct phipm_handle {
   HostBuf res_host, probs_host;
   int grid_blocks[3] = {0, 0, 0};    // cooperative grid size per precision
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the solver kernel
+  DevBuf trace;                      // attempt records
+  long long trace_cap = 0;
+  long long trace_last = 0;          // records produced by the last solve call
+  HostBuf trace_count_host;
+  DevBuf mlp_blob, mlp_part;         // learned controller weights; training partials
+  bool has_mlp = false;
+  // batched form: the launch sequence captured once as a CUDA graph, replayed on gstream
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
 };
 
 static phipm_status fail(phipm_handle* h, phipm_status st, const std::string& msg) {
@@ -204,12 +215,19 @@ extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* par
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve_grid<float>, PM_THREADS, smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve_grid<df32>, PM_THREADS, smem);
   for (int i = 0; i < 3; ++i) h->grid_blocks[i] = std::max(1, occ[i]) * h->num_sms;
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)) !=
+      cudaSuccess) {
+    delete h;
+    return PHIPM_ECUDA;
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess) {
     delete h;
     return PHIPM_ECUDA;
   }
   if (!h->sync.ensure(4096) || !h->res.ensure(sizeof(DevResult)) || !h->res_host.ensure(sizeof(DevResult)) ||
-      !h->expm.ensure(PM_EXPM_DOUBLES * sizeof(double))) {
+      !h->expm.ensure(PM_EXPM_DOUBLES * sizeof(double)) || !h->trace_count_host.ensure(sizeof(unsigned long long))) {
     delete h;
     return PHIPM_ENOMEM;
   }
@@ -220,12 +238,17 @@ extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* par
 extern "C" void phipm_destroy(phipm_handle* h) {
   if (!h) return;
   DevBuf* bufs[] = {&h->ws, &h->sync, &h->partials, &h->expm, &h->conv, &h->res, &h->probs,
-                    &h->order, &h->h_rowptr, &h->h_colind, &h->h_vals, &h->h_b, &h->h_u};
+                    &h->order, &h->h_rowptr, &h->h_colind, &h->h_vals, &h->h_b, &h->h_u,
+                    &h->trace, &h->mlp_blob, &h->mlp_part};
   for (DevBuf* b : bufs) b->release();
   h->res_host.release();
   h->probs_host.release();
+  h->trace_count_host.release();
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->gev) cudaEventDestroy(h->gev);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   delete h;
 }
 
@@ -244,6 +267,7 @@ extern "C" phipm_status phipm_set_params(phipm_handle* h, const phipm_params* pa
 // ------------------------------------------------------------------------------------
 static DevParams make_params(const phipm_params& p) {
   DevParams d;
+  memset(&d, 0, sizeof(d));      // padding too: the batched form keys its captured graph on these bytes
   d.gamma = p.gamma;
   d.delta = p.delta;
   d.theta13 = p.theta13;
@@ -253,6 +277,10 @@ static DevParams make_params(const phipm_params& p) {
   d.max_steps = p.max_steps;
   d.max_rejects = p.max_rejects;
   d.timeout_cycles = p.timeout_cycles;
+  d.mlp = nullptr;
+  d.trace = nullptr;
+  d.trace_count = nullptr;
+  d.trace_cap = 0;
   // [13/13] Pade coefficients of e^x, c_j = (26-j)! 13! / (26! j! (13-j)!), from their closed form
   double c = 1.0;
   for (int j = 0; j <= 13; ++j) {
@@ -403,6 +431,29 @@ static int queue_occupancy(int precision) {
   return std::max(1, occ);
 }
 
+// Attach the learned controller and the trace buffer of the handle to a launch.
+static phipm_status attach_runtime(phipm_handle* h, DevParams& prm, cudaStream_t stream) {
+  if (h->params.controller == 1) {
+    if (!h->has_mlp) return fail(h, PHIPM_EINVAL, "controller = 1 needs phipm_set_controller_weights");
+    prm.mlp = (const float*)h->mlp_blob.p;
+  }
+  if (h->trace_cap > 0) {
+    prm.trace = (TraceRec*)h->trace.p;
+    prm.trace_count = (unsigned long long*)((char*)h->sync.p + 3072);
+    prm.trace_cap = h->trace_cap;
+    cudaError_t e = cudaMemsetAsync(prm.trace_count, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "trace reset");
+  }
+  return PHIPM_OK;
+}
+
+// After the solver kernel: fetch the number of trace records (host copy is read after the sync).
+static cudaError_t fetch_trace_count(phipm_handle* h, const DevParams& prm, cudaStream_t stream) {
+  if (!prm.trace) return cudaSuccess;
+  return cudaMemcpyAsync(h->trace_count_host.p, prm.trace_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                         stream);
+}
+
 // Problems below this size run on one CTA; larger ones on every SM.
 static const int kGridMinN = 16384;
 
@@ -426,6 +477,8 @@ static bool assign_conversions(phipm_handle* h, DevProblem* probs, int count, in
   }
   return true;
 }
+
+static int conv_blocks(long long nnz) { return (int)std::max(1ll, std::min(4096ll, (nnz + 255) / 256)); }
 
 static bool any_csr(const DevProblem* probs, int count) {
   for (int i = 0; i < count; ++i)
@@ -468,7 +521,9 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
   for (int k = 0; k <= p; ++k) P.b[k] = b[k];
   P.u = u;
   if (!assign_conversions(h, &P, 1, prec)) return fail(h, PHIPM_ENOMEM, "value conversion buffer");
-  const DevParams prm = make_params(h->params);
+  DevParams prm = make_params(h->params);
+  st = attach_runtime(h, prm, stream);
+  if (st != PHIPM_OK) return st;
   const int M1 = h->params.m_max + 1;
   DevResult* res_h = (DevResult*)h->res_host.p;
   DevResult* res_d = (DevResult*)h->res.p;
@@ -490,7 +545,7 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
       memcpy(h->probs_host.p, &P, sizeof(P));
       if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, sizeof(P), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return cuda_fail(h, e, "descriptor upload");
-      k_convert_values<<<1, 1024, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
+      k_convert_values<<<dim3(conv_blocks(P.A.nnz), 1), 256, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
     }
     PmWork w{(double*)h->partials.p, (double*)h->expm.p};
@@ -522,7 +577,7 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
         (e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess)
       return cuda_fail(h, e, "descriptor upload");
     if (convert) {
-      k_convert_values<<<1, 1024, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
+      k_convert_values<<<dim3(conv_blocks(P.A.nnz), 1), 256, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
     }
     cudaEventRecord(h->ev0, stream);
@@ -533,7 +588,9 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
   }
   if ((e = cudaMemcpyAsync(res_h, res_d, sizeof(DevResult), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
     return cuda_fail(h, e, "result copy");
+  if ((e = fetch_trace_count(h, prm, stream)) != cudaSuccess) return cuda_fail(h, e, "trace count");
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "solve");
+  if (prm.trace) h->trace_last = (long long)*(unsigned long long*)h->trace_count_host.p;
   if (stats) {
     float kms = 0.f;
     cudaEventElapsedTime(&kms, h->ev0, h->ev1);
@@ -649,28 +706,66 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(pb + ob) ||
       !h->res_host.ensure(rb))
     return fail(h, PHIPM_ENOMEM, "descriptors");
+  for (int i = 0; i < count; ++i) probs[i].id = i;
   memcpy(h->probs_host.p, probs.data(), pb);
   memcpy((char*)h->probs_host.p + pb, order.data(), ob);
-  const DevParams prm = make_params(h->params);
+  DevParams prm = make_params(h->params);
+  {
+    const phipm_status st = attach_runtime(h, prm, stream);
+    if (st != PHIPM_OK) return st;
+  }
   int* queue = (int*)((char*)h->sync.p + 2048);
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(h->probs.p, h->probs_host.p, pb, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + pb, ob, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(queue, 0, sizeof(int), stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(h->res.p, 0, rb, stream)) != cudaSuccess)
-    return cuda_fail(h, e, "descriptor upload");
-  if (prec != PHIPM_F64 && any_csr(probs.data(), count)) {
-    k_convert_values<<<count, 256, 0, stream>>>((const DevProblem*)h->probs.p, count, prec);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
+  long long max_nnz = 0;
+  for (int i = 0; i < count; ++i) max_nnz = std::max(max_nnz, probs[i].A.kind == 0 ? probs[i].A.nnz : 0ll);
+  const bool convert = prec != PHIPM_F64 && any_csr(probs.data(), count);
+  // Everything baked into the graph: sizes, buffers, launch shape and parameters.
+  // Descriptors are read from pinned host memory at every replay.
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* p, size_t n) { key.insert(key.end(), (const unsigned char*)p, (const unsigned char*)p + n); };
+  const void* ptrs[] = {h->probs.p, h->probs_host.p, h->order.p, h->res.p, h->res_host.p, h->ws.p, h->sync.p,
+                        h->trace_count_host.p};
+  put(ptrs, sizeof(ptrs));
+  put(&count, sizeof(count));
+  put(&slots, sizeof(slots));
+  put(&lay, sizeof(lay));
+  put(&prec, sizeof(prec));
+  put(&convert, sizeof(convert));
+  put(&max_nnz, sizeof(max_nnz));
+  put(&prm, sizeof(prm));
+  if (!h->gexec || key != h->gkey) {
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(h, e, "graph capture");
+    cudaStream_t gs = h->gstream;
+    cudaMemcpyAsync(h->probs.p, h->probs_host.p, pb, cudaMemcpyHostToDevice, gs);
+    cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + pb, ob, cudaMemcpyHostToDevice, gs);
+    cudaMemsetAsync(queue, 0, sizeof(int), gs);
+    cudaMemsetAsync(h->res.p, 0, rb, gs);
+    if (prm.trace) cudaMemsetAsync(prm.trace_count, 0, sizeof(unsigned long long), gs);
+    if (convert)
+      k_convert_values<<<dim3(conv_blocks(max_nnz) / 8 + 1, count), 256, 0, gs>>>((const DevProblem*)h->probs.p,
+                                                                                 count, prec);
+    launch_queue_any(prec, slots, gs, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
+                     (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+    cudaMemcpyAsync(h->res_host.p, h->res.p, rb, cudaMemcpyDeviceToHost, gs);
+    fetch_trace_count(h, prm, gs);
+    e = cudaStreamEndCapture(h->gstream, &graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "graph instantiate"); }
+    h->gkey = key;
   }
-  cudaEventRecord(h->ev0, stream);
-  e = launch_queue_any(prec, slots, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
-                       (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
-  if (e != cudaSuccess) return cuda_fail(h, e, "launch");
-  cudaEventRecord(h->ev1, stream);
-  if ((e = cudaMemcpyAsync(h->res_host.p, h->res.p, rb, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-    return cuda_fail(h, e, "result copy");
-  if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(h, e, "batched solve");
+  // order after the caller's stream, replay, wait
+  if ((e = cudaEventRecord(h->gev, stream)) != cudaSuccess || (e = cudaStreamWaitEvent(h->gstream, h->gev, 0)) != cudaSuccess)
+    return cuda_fail(h, e, "stream order");
+  cudaEventRecord(h->ev0, h->gstream);
+  if ((e = cudaGraphLaunch(h->gexec, h->gstream)) != cudaSuccess) return cuda_fail(h, e, "graph launch");
+  cudaEventRecord(h->ev1, h->gstream);
+  if ((e = cudaStreamSynchronize(h->gstream)) != cudaSuccess) return cuda_fail(h, e, "batched solve");
+  if (prm.trace) h->trace_last = (long long)*(unsigned long long*)h->trace_count_host.p;
   float kms = 0.f;
   cudaEventElapsedTime(&kms, h->ev0, h->ev1);
   const DevResult* rh = (const DevResult*)h->res_host.p;
@@ -683,6 +778,97 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   }
   if (overall != PHIPM_OK) return fail(h, overall, status_text(overall));
   return PHIPM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// traces and the learned controller
+// ------------------------------------------------------------------------------------
+static_assert(sizeof(TraceRec) == sizeof(phipm_trace_record), "trace record layout");
+
+extern "C" phipm_status phipm_trace_enable(phipm_handle* h, int64_t capacity) {
+  if (!h) return PHIPM_EINVAL;
+  if (capacity < 0) return fail(h, PHIPM_EINVAL, "capacity < 0");
+  if (capacity > 0 && !h->trace.ensure((size_t)capacity * sizeof(TraceRec))) return fail(h, PHIPM_ENOMEM, "trace buffer");
+  h->trace_cap = capacity;
+  h->trace_last = 0;
+  return PHIPM_OK;
+}
+
+extern "C" phipm_status phipm_trace_read(phipm_handle* h, phipm_trace_record* out, int64_t max, int64_t* count) {
+  if (!h || (max > 0 && !out)) return PHIPM_EINVAL;
+  if (count) *count = h->trace_last;
+  const long long k = std::min<long long>(std::min<long long>(max, h->trace_last), h->trace_cap);
+  if (k <= 0) return PHIPM_OK;
+  cudaError_t e = cudaMemcpy(out, h->trace.p, (size_t)k * sizeof(TraceRec), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "trace copy");
+  return PHIPM_OK;
+}
+
+extern "C" phipm_status phipm_set_controller_weights(phipm_handle* h, const float* blob, size_t count) {
+  if (!h) return PHIPM_EINVAL;
+  if (count == 0) { h->has_mlp = false; return PHIPM_OK; }
+  if (!blob || count != (size_t)PHIPM_CONTROLLER_FLOATS)
+    return fail(h, PHIPM_EINVAL, "controller blob must hold PHIPM_CONTROLLER_FLOATS floats");
+  for (size_t i = 0; i < count; ++i)
+    if (!std::isfinite(blob[i])) return fail(h, PHIPM_EINVAL, "controller blob is not finite");
+  for (int i = 0; i < MLP_IN; ++i)
+    if (!(blob[MLP_NP + MLP_IN + i] > 0.f)) return fail(h, PHIPM_EINVAL, "feature scales must be positive");
+  if (!h->mlp_blob.ensure(count * sizeof(float))) return fail(h, PHIPM_ENOMEM, "controller weights");
+  cudaError_t e = cudaMemcpy(h->mlp_blob.p, blob, count * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(h, e, "controller weights");
+  h->has_mlp = true;
+  return PHIPM_OK;
+}
+
+static int mlp_blocks(phipm_handle* h, long long n) {
+  const long long want = (n + MLP_WARPS * 4 - 1) / (MLP_WARPS * 4);
+  return (int)std::max(1ll, std::min<long long>(want, h->num_sms));
+}
+
+extern "C" phipm_status phipm_mlp_forward(phipm_handle* h, const float* w, const float* X, int64_t n, float* Y,
+                                         void* stream_) {
+  if (!h || n < 0 || (n > 0 && (!w || !X || !Y))) return PHIPM_EINVAL;
+  if (n == 0) return PHIPM_OK;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const int G = (int)std::max(1ll, std::min<long long>((n + 7) / 8, 4ll * h->num_sms));
+  k_mlp_forward<<<G, 256, 0, stream>>>(w, X, n, Y);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  return e == cudaSuccess ? PHIPM_OK : cuda_fail(h, e, "mlp forward");
+}
+
+extern "C" phipm_status phipm_mlp_grad(phipm_handle* h, const float* w, const float* X, const float* T, int64_t n,
+                                      float* grad, float* loss, void* stream_) {
+  if (!h || n <= 0 || !w || !X || !T || !grad) return PHIPM_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const int G = mlp_blocks(h, n);
+  if (!h->mlp_part.ensure((size_t)G * MLP_PART * sizeof(float))) return fail(h, PHIPM_ENOMEM, "mlp partials");
+  k_mlp_grad<<<G, MLP_WARPS * 32, sizeof(MlpSmem), stream>>>(w, X, T, n, (float*)h->mlp_part.p);
+  k_mlp_adam<<<(MLP_NP + 256) / 256, 256, 0, stream>>>(nullptr, nullptr, nullptr, (const float*)h->mlp_part.p, G,
+                                                       grad, loss, 0, 0.f, 0.f, 0.f, 0.f);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  return e == cudaSuccess ? PHIPM_OK : cuda_fail(h, e, "mlp gradient");
+}
+
+extern "C" phipm_status phipm_mlp_train(phipm_handle* h, float* w, float* m, float* v, const float* X, const float* T,
+                                       int64_t n, int32_t iters, int64_t t0, float lr, float* losses, void* stream_) {
+  if (!h || n <= 0 || iters < 0 || !w || !m || !v || !X || !T || !(lr > 0.f)) return PHIPM_EINVAL;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const int G = mlp_blocks(h, n);
+  if (!h->mlp_part.ensure((size_t)G * MLP_PART * sizeof(float) + (size_t)std::max(iters, 1) * sizeof(float)))
+    return fail(h, PHIPM_ENOMEM, "mlp partials");
+  float* lossdev = (float*)((char*)h->mlp_part.p + (size_t)G * MLP_PART * sizeof(float));
+  for (int it = 0; it < iters; ++it) {
+    k_mlp_grad<<<G, MLP_WARPS * 32, sizeof(MlpSmem), stream>>>(w, X, T, n, (float*)h->mlp_part.p);
+    k_mlp_adam<<<(MLP_NP + 256) / 256, 256, 0, stream>>>(w, m, v, (const float*)h->mlp_part.p, G, nullptr,
+                                                         lossdev + it, t0 + it + 1, lr, 0.9f, 0.999f, 1e-8f);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && losses && iters > 0)
+    e = cudaMemcpyAsync(losses, lossdev, (size_t)iters * sizeof(float), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  return e == cudaSuccess ? PHIPM_OK : cuda_fail(h, e, "mlp training");
 }
 
 // ------------------------------------------------------------------------------------

@@ -36,16 +36,28 @@ struct DevOp {
   df32 cc2, cm2[3], cp2[3];   // stencil coefficients as float pairs (hi alone for FP32)
 };
 
+// One attempt record; the same layout as phipm_trace_record in include/phipm.h.
+struct TraceRec {
+  int problem, step, attempt, accepted, m_req, m_used, p, n;
+  double t, t_end, tau, eps, omega, norm_a, tol;
+  int source, rejects_prev;
+};
+
 struct DevParams {
   double gamma, delta, theta13, breakdown_tol;
   int m_init, m_max;
   long long max_steps, max_rejects;
   long long timeout_cycles;
   double pade_b[14];     // degree-13 Pade coefficients, computed on the host from their closed form
+  const float* mlp;      // learned-controller blob (device), or null
+  TraceRec* trace;       // attempt records (device), or null
+  unsigned long long* trace_count;
+  long long trace_cap;
 };
 
 struct DevProblem {
   DevOp A;
+  int id;                // index of the problem in the call (traces)
   int p;
   int symm;              // -1 detect, 0, 1
   double t_end, tol;

@@ -6,21 +6,31 @@
 // without a broadcast.
 #pragma once
 #include "phipm_common.cuh"
+#include "phipm_mlp.cuh"
 
 // FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
+#define PM_DRED 512                    // partials of one dot pass: PM_WARPS warps x PM_DSEG segments
+// The learned controller proposes (tau, m) for the first PM_LEARNED_STEPS steps of a
+// solve only; afterwards the paper's controller runs alone.  A network that keeps
+// proposing steps smaller than it needs to (or m too small) can therefore cost at most
+// that many steps before the paper's controller, whose tau grows geometrically when
+// omega is small (Eq. taunew), takes over.
+#define PM_LEARNED_STEPS 48
 
 // Scalar state of one problem.  Thread 0 writes it, every thread reads it after
 // the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
 // would cost a warp-wide FP64 instruction per warp on a pipe of about 2 FMA/clk/SM.
 struct PmScal {
   double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
-  double fnorm, last_tau;
+  double fnorm, last_tau, omega, last_omega;
   double tl[PM_MAXP + 1];
   df32 inv2;
   float invf;
   int m, m_used, kcur, invariant, sq, nonfinite, nvv, measure, outcome, status, go, symmetric, lanczos, last_m;
-  long long steps, rejects, expms;
+  int m_req, attempt, source, step_rejects, prev_rejects;
+  long long steps, rejects, expms, trace_idx;
+  float feat[MLP_IN];
 };
 
 // per-CTA shared state
@@ -36,8 +46,9 @@ struct PmShared {
   double ucoef[PM_NSLOT + PM_MAXP + 1];
   float ucf[PM_NSLOT];
   df32 ucd[PM_NSLOT];
-  double dred[PM_NSLOT + PM_WARPS + 2];
+  double dred[PM_DRED];                // per-segment partial dots of one pass
   double wy[PM_WARPS][PM_NA];          // per-warp column of the exponential's solve
+  float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
 };
 
@@ -222,48 +233,83 @@ __device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
 // Gram-Schmidt passes over this CTA's rows [lo, hi)
 // ------------------------------------------------------------------------------------
 // d_i = sum_r V[i][r] y[r], i < nv, into s.coef[0..nv); with_norm adds sum y^2
-// as s.coef[nv].  Work is split into units (vector, row chunk), one warp each,
-// so the cross-lane sum runs once per unit.  lo is a multiple of 64 and vectors
-// are 256-byte aligned, so every chunk starts on a 16-byte boundary.
+// as s.coef[nv].  The nvec x rows products, taken vector after vector, are cut
+// into PM_WARPS equal contiguous runs, one per warp, so every warp streams a long
+// run (four 16-byte loads of V and of y per lane in flight) whatever nvec is.  A
+// run crosses at most a few vector boundaries; each piece (segment) leaves one
+// warp-reduced partial in s.dred, and d_i sums the partials of its segments in
+// warp order (deterministic).  Rows of vectors are 256-byte aligned from lo, a
+// multiple of 64, so quads start on row offsets that are multiples of 4.
+#define PM_DSEG (PM_DRED / PM_WARPS)   // segments per warp
+template <class S>
+__device__ __forceinline__ double dot_segment(const S* __restrict__ v, const S* __restrict__ y, int a, int b) {
+  typedef Elem<S> E;
+  typedef typename E::Acc Acc;
+  const int lane = threadIdx.x & 31;
+  Acc acc0 = E::zero(), acc1 = E::zero();
+  const int qa = min(b, (a + 3) & ~3);      // quads cover [qa, qb)
+  const int qb = max(qa, b & ~3);
+  if (a + lane < qa) E::dot(acc1, v[a + lane], y[a + lane]);        // head: at most 3 rows
+  int e = qa + 4 * lane;
+  for (; e + 384 + 3 < qb; e += 512) {
+    Quad<S> v0, y0, v1, y1, v2, y2, v3, y3;
+    v0.load(v + e); y0.load(y + e);
+    v1.load(v + e + 128); y1.load(y + e + 128);
+    v2.load(v + e + 256); y2.load(y + e + 256);
+    v3.load(v + e + 384); y3.load(y + e + 384);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      E::dot(acc0, v0.x[k], y0.x[k]);
+      E::dot(acc1, v1.x[k], y1.x[k]);
+      E::dot(acc0, v2.x[k], y2.x[k]);
+      E::dot(acc1, v3.x[k], y3.x[k]);
+    }
+  }
+  for (; e + 3 < qb; e += 128) {
+    Quad<S> v0, y0;
+    v0.load(v + e); y0.load(y + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) E::dot(acc0, v0.x[k], y0.x[k]);
+  }
+  if (qb + lane < b) E::dot(acc0, v[qb + lane], y[qb + lane]);      // tail: at most 3 rows
+  return E::val(acc0) + E::val(acc1);
+}
+
 template <class S>
 __device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo, int hi,
                          bool with_norm, PmShared& s) {
   typedef Elem<S> E;
-  typedef typename E::Acc Acc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rows = hi - lo;
+  const long long rows = hi - lo;
   const int nvec = nv + (with_norm ? 1 : 0);
-  int cpv = (PM_WARPS + nvec - 1) / nvec;                 // chunks per vector
-  cpv = max(1, min(cpv, (rows + 255) / 256));
-  const int units = nvec * cpv;
-  const int chunk = (((rows + cpv - 1) / cpv) + 127) & ~127;
-  for (int un = warp; un < units; un += PM_WARPS) {
-    const int i = un / cpv, c = un - i * cpv;
-    const int a = lo + c * chunk;
-    const int b = min(hi, a + chunk);
-    const S* v = (i < nv) ? V + (size_t)i * ld : y;
-    Acc acc0 = E::zero(), acc1 = E::zero();
-    int e = a + 4 * lane;
-    for (; e + 128 + 3 < b; e += 256) {
-      Quad<S> v0, y0, v1, y1;
-      v0.load(v + e); y0.load(y + e); v1.load(v + e + 128); y1.load(y + e + 128);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { E::dot(acc0, v0.x[k], y0.x[k]); E::dot(acc1, v1.x[k], y1.x[k]); }
+  const long long total = (long long)nvec * rows;
+  if (total == 0) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    __syncthreads();
+    return;
+  }
+  // run length, a multiple of 4 rows.  A run meets at most run / rows + 2 vectors,
+  // and run <= nvec rows / 16 + 4 rows with nvec <= 65 keeps that below 12 <= PM_DSEG.
+  const long long run = (((total + PM_WARPS - 1) / PM_WARPS) + 3) & ~3ll;
+  long long f = (long long)warp * run;
+  const long long fend = min(total, f + run);
+  if (f < fend) {
+    int i = (int)(f / rows);                 // first vector of this run
+    long long r0 = f - (long long)i * rows;
+    for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
+      const long long r1 = min(rows, r0 + (fend - f));
+      const S* v = (i < nv) ? V + (size_t)i * ld : y;
+      const double d = pm_warp_sum(dot_segment<S>(v, y, lo + (int)r0, lo + (int)r1));
+      if (lane == 0) s.dred[warp * PM_DSEG + seg] = d;
+      f += r1 - r0;
     }
-    for (; e + 3 < b; e += 128) {
-      Quad<S> v0, y0;
-      v0.load(v + e); y0.load(y + e);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) E::dot(acc0, v0.x[k], y0.x[k]);
-    }
-    for (int r = e; r < b && r < e + 4; ++r) E::dot(acc1, v[r], y[r]);
-    const double d = pm_warp_sum(E::val(acc0) + E::val(acc1));
-    if (lane == 0) s.dred[un] = d;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    const long long fa = (long long)i * rows, fb = fa + rows - 1;
     double t = 0.0;
-    for (int c = 0; c < cpv; ++c) t += s.dred[i * cpv + c];
+    for (long long w = fa / run; w <= fb / run && w < PM_WARPS; ++w)
+      t += s.dred[w * PM_DSEG + (int)(i - (w * run) / rows)];
     s.coef[i] = t;
   }
   __syncthreads();
@@ -286,15 +332,22 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[k] = f2_zero();
         int i = 0;
-        for (; i + 1 < nv; i += 2) {
-          Quad<S> v0, v1;
+        for (; i + 3 < nv; i += 4) {          // four basis quads in flight
+          Quad<S> v0, v1, v2, v3;
           v0.load(V + (size_t)i * ld + r);
           v1.load(V + (size_t)(i + 1) * ld + r);
-          const df32 h0 = h[i], h1 = h[i + 1];
+          v2.load(V + (size_t)(i + 2) * ld + r);
+          v3.load(V + (size_t)(i + 3) * ld + r);
+          const df32 h0 = h[i], h1 = h[i + 1], h2 = h[i + 2], h3 = h[i + 3];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) { f2_add_prod(acc[k], h0, v0.x[k]); f2_add_prod(acc[k], h1, v1.x[k]); }
+          for (int k = 0; k < 4; ++k) {
+            f2_add_prod(acc[k], h0, v0.x[k]);
+            f2_add_prod(acc[k], h1, v1.x[k]);
+            f2_add_prod(acc[k], h2, v2.x[k]);
+            f2_add_prod(acc[k], h3, v3.x[k]);
+          }
         }
-        if (i < nv) {
+        for (; i < nv; ++i) {
           Quad<S> v0;
           v0.load(V + (size_t)i * ld + r);
           const df32 h0 = h[i];
@@ -308,15 +361,22 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) b.x[k] = S(0);
         int i = 0;
-        for (; i + 1 < nv; i += 2) {
-          Quad<S> v0, v1;
+        for (; i + 3 < nv; i += 4) {
+          Quad<S> v0, v1, v2, v3;
           v0.load(V + (size_t)i * ld + r);
           v1.load(V + (size_t)(i + 1) * ld + r);
-          const S h0 = h[i], h1 = h[i + 1];
+          v2.load(V + (size_t)(i + 2) * ld + r);
+          v3.load(V + (size_t)(i + 3) * ld + r);
+          const S h0 = h[i], h1 = h[i + 1], h2 = h[i + 2], h3 = h[i + 3];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) { a.x[k] = fma(-h0, v0.x[k], a.x[k]); b.x[k] = fma(-h1, v1.x[k], b.x[k]); }
+          for (int k = 0; k < 4; ++k) {
+            a.x[k] = fma(-h0, v0.x[k], a.x[k]);
+            b.x[k] = fma(-h1, v1.x[k], b.x[k]);
+            a.x[k] = fma(-h2, v2.x[k], a.x[k]);
+            b.x[k] = fma(-h3, v3.x[k], b.x[k]);
+          }
         }
-        if (i < nv) {
+        for (; i < nv; ++i) {
           Quad<S> v0;
           v0.load(V + (size_t)i * ld + r);
           const S h0 = h[i];
@@ -695,6 +755,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     }
     c.t = 0.0;
     c.nonfinite = 0;
+    c.last_omega = 1.0;
+    c.prev_rejects = 0;
+    c.step_rejects = 0;
   }
   __syncthreads();
   if (!c.go) {        // every b_k = 0: u = 0
@@ -743,13 +806,46 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       c.kcur = 0;          // Arnoldi / Lanczos steps done for this w_p
       c.invariant = 0;     // happy breakdown reached
       c.hn = 0.0;          // ||y|| of the last step (h_{kcur+1,kcur})
+      c.attempt = 0;
+      c.source = 0;
       ctl_reset(ctl);
+    }
+    __syncthreads();
+    if (prm.mlp != nullptr && c.steps < PM_LEARNED_STEPS && tid < 32) {
+      // learned controller (a11): propose (tau, m) for the first attempt of this step
+      const float* blob = prm.mlp;
+      if (tid == 0) {
+        const double raw[MLP_IN] = {log10(c.normA * c.t_end), log10(c.tol), (double)p, log10(c.tau * c.normA),
+                                    c.m / 64.0, log10(fmax(c.last_omega, 1e-6)), (double)c.prev_rejects,
+                                    log10((double)n)};
+        for (int i = 0; i < MLP_IN; ++i)
+          c.feat[i] = (float)((raw[i] - blob[MLP_NP + i]) / blob[MLP_NP + MLP_IN + i]);
+      }
+      __syncwarp();
+      float x[MLP_IN];
+      bool ok = true;
+      for (int i = 0; i < MLP_IN; ++i) { x[i] = c.feat[i]; ok = ok && isfinite(x[i]); }
+      if (ok) {
+        float y[MLP_OUT];
+        mlp_warp_forward(blob, x, s.mh[0], s.mh[1], y);
+        if (tid == 0) {
+          const double lr = (double)y[0] * blob[MLP_NP + 2 * MLP_IN + 2] + blob[MLP_NP + 2 * MLP_IN];
+          const double mm = (double)y[1] * blob[MLP_NP + 2 * MLP_IN + 3] + blob[MLP_NP + 2 * MLP_IN + 1];
+          if (isfinite(lr) && isfinite(mm)) {
+            const double ratio = exp2(fmin(fmax(lr, -5.0), 3.0));
+            c.tau = fmin(c.tau * ratio, c.t_end - c.t);
+            c.m = (int)fmin(fmax(rint(64.0 * mm), 1.0), (double)prm.m_max);
+            c.source = 1;
+          }
+        }
+      }
     }
     __syncthreads();
     const double* wp = (p == 0) ? u : W + (size_t)(p - 1) * ld;
     for (;;) {   // attempts of one step (Algorithm 3, inner loop)
       if (tid == 0) {
         c.tau_used = c.tau;
+        c.m_req = c.m;
         c.m_used = c.m;
         c.eps = 0.0;
         c.hlast = 0.0;
@@ -904,6 +1000,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           c.eps = pow(c.tau_used, p + 1) * c.beta * fabs(c.hlast) * fabs(s.phi1[mu - 1]);   // Eq. (errest), R4
         }
         if (!isfinite(c.eps)) {
+          c.omega = c.eps;
           c.nonfinite += 1;
           c.rejects += 1;
           c.outcome = PM_ATT_RETRY;
@@ -916,6 +1013,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           int m = mu;
           const int m_max = prm.m_max;
           const double omega = c.t_end * eps / (tau_used * c.tol);          // Eq. (taunew)
+          c.omega = omega;
           // Algorithm 4
           double q;
           bool qf;
@@ -959,13 +1057,15 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           };
           const double c_tau = ceil(t_left / tau_new) * C1((double)m);
           const double c_m = ceil(t_left / tau_used) * C1((double)m_new);
+          // m within a factor 4/3 of the current one and within [1, m_max]; when that
+          // leaves m as it is (m at a bound), only a change of tau can alter the attempt
+          const int m_cand = min(min(max(max(m_new, (3 * m) / 4), 1), (4 * m + 2) / 3), m_max);
           bool branch_tau;
-          if (c_tau < c_m) {
+          if (c_tau < c_m || m_cand == m) {
             c.tau = fmin(fmin(fmax(tau_new, tau_used / 5.0), 2.0 * tau_used), t_left);
             branch_tau = true;
           } else {
-            int mm = max(max(m_new, (3 * m) / 4), 1);
-            m = min(min(mm, (4 * m + 2) / 3), m_max);
+            m = m_cand;
             branch_tau = false;
           }
           c.m = m;
@@ -1001,6 +1101,35 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             ctl.m_old = mu;
           }
         }
+        // attempt record (G15): written by one CTA of the team
+        c.trace_idx = -1;
+        if (prm.trace != nullptr && team.rank() == 0) {
+          const unsigned long long idx = atomicAdd(prm.trace_count, 1ull);
+          if ((long long)idx < prm.trace_cap) {
+            TraceRec& tr = prm.trace[idx];
+            tr.problem = P.id;
+            tr.step = (int)c.steps;
+            tr.attempt = c.attempt;
+            tr.accepted = (c.outcome == PM_ATT_ACCEPT) ? 1 : 0;
+            tr.m_req = c.m_req;
+            tr.m_used = mu;
+            tr.p = p;
+            tr.n = n;
+            tr.t = c.t;
+            tr.t_end = c.t_end;
+            tr.tau = c.tau_used;
+            tr.eps = c.eps;
+            tr.omega = c.omega;
+            tr.norm_a = c.normA;
+            tr.tol = c.tol;
+            tr.source = c.source;
+            tr.rejects_prev = c.prev_rejects;
+            c.trace_idx = (long long)idx;
+          }
+        }
+        c.attempt += 1;
+        c.source = 0;
+        if (c.outcome != PM_ATT_ACCEPT) c.step_rejects += 1;
       }
       __syncthreads();
       if (c.outcome == PM_ATT_FAIL) goto done;
@@ -1046,6 +1175,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               if (c.rejects > prm.max_rejects) { c.status = PM_EMAXSTEPS; c.outcome = PM_ATT_FAIL; }
               c.tau = c.tau_used * pow(0.5 * PM_F32_AMP * unew / c.fnorm, 1.0 / (double)(p - 1));
               c.m = c.m_used;
+              c.step_rejects += 1;
+              if (c.trace_idx >= 0) prm.trace[c.trace_idx].accepted = 0;
               ctl_reset(ctl);
             }
           }
@@ -1063,6 +1194,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           if (c.t < c.t_end) c.tau = fmin(c.tau, c.t_end - c.t);
           c.last_tau = c.tau_used;
           c.last_m = c.m_used;
+          c.last_omega = c.omega;
+          c.prev_rejects = c.step_rejects;
+          c.step_rejects = 0;
         }
         PM_SYNC_OR_FAIL();    // u complete before the next SpMV reads neighbours; c visible
         if (c.status != PM_OK) goto done;

@@ -1,0 +1,180 @@
+"""The learned (tau, m) controller: data from attempt traces, training on the GPU.
+
+Flow (every numerical step of training and solving runs in libphipm's kernels;
+this module builds arrays and calls the library):
+  1. solve a family of training problems with the paper's controller and
+     attempt traces enabled (phipm_trace_enable);
+  2. turn each accepted step into one example: the features the solver
+     computes at the start of a step, and a hindsight label (tau*, m*), given
+     as log2(tau* / tau the step started with) and m* / 64:
+       - a step with rejected attempts: the accepted (tau, m), which the error
+         estimate has shown to be acceptable;
+       - a step accepted at once: the (tau, m) that the paper's controller
+         proposes right after it (Eq. taunew and the m update of Algorithm 4,
+         from the accepted attempt's error), its estimate of the largest
+         acceptable step.  The accepted tau itself would understate it, and
+         a network trained on it learns to shrink every step.
+     Such a step gives no example when it is the last one of its solve or
+     when the follow-up proposal was cut to the end of the interval;
+  3. standardise, train the 8-64-64-2 GELU network with phipm_mlp_train
+     (full-batch Adam, mean squared error);
+  4. install the blob (weights + standardisation) with
+     phipm_set_controller_weights and solve with params.controller = 1.
+
+The feature definition must match the solver's (csrc/phipm_engine.cuh, learned
+proposal block):
+  log10(||A||_inf t_end), log10(Tol), p, log10(tau_start ||A||_inf), m_start / 64,
+  log10(omega of the previous accepted attempt, floored at 1e-6; 1 before the
+  first step), rejected attempts in the previous step, log10(n).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import workloads as wl
+
+N_FEATURES = 8
+
+
+# --------------------------------------------------------------------------------------
+# training problems: seeded variants of the three single-problem configurations
+# --------------------------------------------------------------------------------------
+def training_problems(count: int = 384, seed0: int = 7000) -> list:
+    """Variants of the 2D Laplacian (config 1), the convection-diffusion family of
+    config 2 (velocities spanning Peclet numbers 1..1e3) and the 3D Laplacian of
+    config 3, at sizes a single CTA solves quickly."""
+    probs = []
+    for i in range(count):
+        s = seed0 + i
+        kind = i % 3
+        u = wl.uniform(s, 1, 6)
+        if kind == 0:
+            N = int(16 + u[0] * 48)
+            p = int(u[1] * 5) % 5
+            t_end = 0.01 * 10 ** (2 * u[2] - 1)
+            tol = 10 ** (-10 + 5 * u[3])
+            st = wl.laplacian(2, N)
+            b = [wl.normal(s, 100 + k, st.n) for k in range(p + 1)]
+            probs.append(wl.Problem(f"tr_lap2_{i}", wl.stencil_to_csr(st), b, t_end, tol, 1, meta=dict(seed=s)))
+        elif kind == 1:
+            N = int(16 + u[0] * 80)
+            p = 1 + int(u[1] * 4) % 4
+            t_end = 1e-3 * 10 ** (2 * u[2] - 1)
+            tol = 10 ** (-10 + 4 * u[3])
+            speed = 10 ** (3 * u[4])
+            ang = 2 * math.pi * u[5]
+            st = wl.convection_diffusion_2d(N, 1.0, speed * math.cos(ang), speed * math.sin(ang))
+            b = [wl.normal(s, 100 + k, st.n) for k in range(p + 1)]
+            probs.append(wl.Problem(f"tr_cd_{i}", wl.stencil_to_csr(st), b, t_end, tol, 0, meta=dict(seed=s)))
+        else:
+            N = int(8 + u[0] * 14)
+            p = int(u[1] * 4) % 4
+            t_end = 1e-4 * 10 ** (2 * u[2] - 1)
+            tol = 10 ** (-9 + 4 * u[3])
+            st = wl.laplacian(3, N)
+            b = [wl.uniform(s, 100 + k, st.n, -1.0, 1.0) for k in range(p + 1)]
+            probs.append(wl.Problem(f"tr_lap3_{i}", wl.stencil_to_csr(st), b, t_end, tol, 1, meta=dict(seed=s)))
+    return probs
+
+
+# --------------------------------------------------------------------------------------
+# traces -> examples
+# --------------------------------------------------------------------------------------
+def examples_from_traces(records: list) -> tuple:
+    """(X_raw [k x 8], T_raw [k x 2]) from attempt records of one or more solves."""
+    by_prob: dict = {}
+    for r in records:
+        by_prob.setdefault(r["problem"], []).append(r)
+    X, T = [], []
+    for prob, recs in by_prob.items():
+        steps: dict = {}
+        for r in recs:
+            steps.setdefault(r["step"], []).append(r)
+        omega_prev = 1.0
+        order = sorted(steps)
+        for k in order:
+            att = sorted(steps[k], key=lambda r: r["attempt"])
+            acc = [r for r in att if r["accepted"]]
+            if not acc:
+                continue
+            r0, ra = att[0], acc[-1]
+            nxt = steps.get(k + 1)
+            rn = min(nxt, key=lambda r: r["attempt"]) if nxt else None
+            na = r0["norm_a"]
+            if len(att) > 1:
+                label = (ra["tau"], ra["m_used"])
+            elif (rn is not None and rn["attempt"] == 0 and rn["tau"] > 0
+                  and rn["t"] + rn["tau"] < rn["t_end"] * (1.0 - 1e-12)):
+                label = (rn["tau"], rn["m_req"])
+            else:
+                label = None
+            if label is not None and r0["attempt"] == 0 and na > 0 and r0["tau"] > 0:
+                x = [math.log10(na * r0["t_end"]), math.log10(r0["tol"]), float(r0["p"]),
+                     math.log10(r0["tau"] * na), r0["m_req"] / 64.0, math.log10(max(omega_prev, 1e-6)),
+                     float(r0["rejects_prev"]), math.log10(r0["n"])]
+                t = [math.log2(label[0] / r0["tau"]), label[1] / 64.0]
+                if all(math.isfinite(v) for v in x + t):
+                    X.append(x)
+                    T.append(t)
+            omega_prev = ra["omega"] if math.isfinite(ra["omega"]) else 1.0
+    return np.asarray(X, dtype=np.float64).reshape(-1, N_FEATURES), np.asarray(T, dtype=np.float64).reshape(-1, 2)
+
+
+def standardise(X: np.ndarray, T: np.ndarray):
+    xm, xs = X.mean(axis=0), X.std(axis=0)
+    xs = np.where(xs < 1e-3, 1.0, xs)
+    ym, ys = T.mean(axis=0), T.std(axis=0)
+    ys = np.where(ys < 1e-3, 1.0, ys)
+    return xm, xs, ym, ys
+
+
+def make_blob(w: np.ndarray, xm, xs, ym, ys) -> np.ndarray:
+    return np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(xm, np.float32), np.asarray(xs, np.float32),
+                           np.asarray(ym, np.float32), np.asarray(ys, np.float32)]).astype(np.float32)
+
+
+def init_weights(seed: int) -> np.ndarray:
+    """Fan-in scaled uniform initialisation from the counter-based generator."""
+    w = np.zeros(4866, dtype=np.float64)
+    w[0:512] = wl.uniform(seed, 1, 512, -1.0, 1.0) * math.sqrt(6.0 / 8)
+    w[576:4672] = wl.uniform(seed, 2, 4096, -1.0, 1.0) * math.sqrt(6.0 / 64)
+    w[4736:4864] = wl.uniform(seed, 3, 128, -1.0, 1.0) * math.sqrt(6.0 / 64) * 0.1
+    return w.astype(np.float32)
+
+
+# --------------------------------------------------------------------------------------
+# GPU steps (library calls)
+# --------------------------------------------------------------------------------------
+def collect_traces(solver, problems: list, chunk: int = 128) -> list:
+    """Solve problems with the paper's controller (batched launches) and return their records."""
+    import torch
+    from . import phipm as pm
+    solver.set_controller(0)
+    solver.trace_enable(1 << 20)
+    records = []
+    for c0 in range(0, len(problems), chunk):
+        part = problems[c0:c0 + chunk]
+        ops = [pm.DeviceOperator(p_.op) for p_ in part]
+        bs = [[torch.as_tensor(x).cuda() for x in p_.b] for p_ in part]
+        solver.solve_batched([p_.t_end for p_ in part], ops, bs, [p_.tol for p_ in part], [p_.symm for p_ in part])
+        for r in solver.trace_read():
+            r = dict(r)
+            r["problem"] += c0
+            records.append(r)
+    solver.trace_enable(0)
+    return records
+
+
+def train(solver, X: np.ndarray, T: np.ndarray, iters: int = 3000, lr: float = 3e-3, seed: int = 11):
+    """Full-batch Adam on standardised data through phipm_mlp_train; returns (blob, losses)."""
+    import torch
+    xm, xs, ym, ys = standardise(X, T)
+    Xn = torch.as_tensor(((X - xm) / xs).astype(np.float32)).cuda().contiguous()
+    Tn = torch.as_tensor(((T - ym) / ys).astype(np.float32)).cuda().contiguous()
+    w = torch.as_tensor(init_weights(seed)).cuda()
+    m = torch.zeros_like(w)
+    v = torch.zeros_like(w)
+    losses = solver.mlp_train(w, m, v, Xn, Tn, iters, 0, lr)
+    return make_blob(w.cpu().numpy(), xm, xs, ym, ys), losses

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE =
 F64, F32_MIXED, F64_PAIR = 0, 1, 2
 OP_CSR, OP_STENCIL = 0, 1
 M_MAX, P_MAX, NOALLOC_MAX_N = 64, 8, 8192
+MLP_PARAMS, CONTROLLER_FLOATS = 4866, 4886
 
 
 class CsrC(ctypes.Structure):
@@ -43,6 +44,13 @@ class StatsC(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TraceRecordC(ctypes.Structure):
+    _fields_ = [("problem", c_int32), ("step", c_int32), ("attempt", c_int32), ("accepted", c_int32),
+                ("m_req", c_int32), ("m_used", c_int32), ("p", c_int32), ("n", c_int32),
+                ("t", c_double), ("t_end", c_double), ("tau", c_double), ("eps", c_double), ("omega", c_double),
+                ("norm_a", c_double), ("tol", c_double), ("source", c_int32), ("rejects_prev", c_int32)]
 
 
 class ParamsC(ctypes.Structure):
@@ -92,6 +100,19 @@ def lib(build_if_needed: bool = True):
     L.phipm_solve_noalloc.argtypes = [c_double, ctypes.POINTER(OperatorC), c_int32, ctypes.POINTER(c_void_p),
                                       c_double, c_int32, c_void_p, ctypes.POINTER(StatsC), c_void_p]
     L.phipm_solve_noalloc.restype = c_int32
+    L.phipm_trace_enable.argtypes = [c_void_p, c_int64]
+    L.phipm_trace_enable.restype = c_int32
+    L.phipm_trace_read.argtypes = [c_void_p, ctypes.POINTER(TraceRecordC), c_int64, ctypes.POINTER(c_int64)]
+    L.phipm_trace_read.restype = c_int32
+    L.phipm_set_controller_weights.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]
+    L.phipm_set_controller_weights.restype = c_int32
+    L.phipm_mlp_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+    L.phipm_mlp_forward.restype = c_int32
+    L.phipm_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
+    L.phipm_mlp_grad.restype = c_int32
+    L.phipm_mlp_train.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
+                                  c_int64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), c_void_p]
+    L.phipm_mlp_train.restype = c_int32
     _LIB = L
     return L
 
@@ -114,14 +135,19 @@ def default_params() -> ParamsC:
 class DeviceOperator:
     """A on the device: CSR arrays as torch tensors (int32 / int32 / float64) or stencil coefficients."""
 
-    def __init__(self, op, device="cuda"):
+    def __init__(self, op, device="cuda", arrays=None):
+        """arrays: optional (rowptr, colind, values) device tensors already holding op's CSR
+        arrays (e.g. views of one packed buffer); otherwise they are copied from op."""
         import torch
         self.src = op
         self.c = OperatorC()
         if hasattr(op, "rowptr"):
-            self.rowptr = torch.as_tensor(np.asarray(op.rowptr, dtype=np.int32)).to(device)
-            self.colind = torch.as_tensor(np.asarray(op.colind, dtype=np.int32)).to(device)
-            self.values = torch.as_tensor(np.asarray(op.values, dtype=np.float64)).to(device)
+            if arrays is not None:
+                self.rowptr, self.colind, self.values = arrays
+            else:
+                self.rowptr = torch.as_tensor(np.asarray(op.rowptr, dtype=np.int32)).to(device)
+                self.colind = torch.as_tensor(np.asarray(op.colind, dtype=np.int32)).to(device)
+                self.values = torch.as_tensor(np.asarray(op.values, dtype=np.float64)).to(device)
             self.c.kind = OP_CSR
             self.c.csr = CsrC(int(op.n), int(self.values.numel()), self.rowptr.data_ptr(), self.colind.data_ptr(),
                               self.values.data_ptr())
@@ -240,6 +266,58 @@ class Phipm:
             self._check(st)
         return out, stats.as_dict(), st
 
+    # ---- attempt traces and the learned controller -------------------------------------
+    def trace_enable(self, capacity: int):
+        self._check(lib().phipm_trace_enable(self.h, int(capacity)))
+
+    def trace_read(self, max_records: int = 1 << 20) -> list:
+        """Attempt records of the last solve call, as dicts."""
+        cnt = c_int64()
+        lib().phipm_trace_read(self.h, None, 0, ctypes.byref(cnt))
+        k = min(int(cnt.value), int(max_records))
+        buf = (TraceRecordC * max(k, 1))()
+        self._check(lib().phipm_trace_read(self.h, buf, k, ctypes.byref(cnt)))
+        return [{f: getattr(buf[i], f) for f, _ in TraceRecordC._fields_} for i in range(k)]
+
+    def set_controller_weights(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.float32)
+        if blob.size == 0:
+            self._check(lib().phipm_set_controller_weights(self.h, None, 0))
+            return
+        self._check(lib().phipm_set_controller_weights(
+            self.h, blob.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), blob.size))
+
+    def set_controller(self, kind: int):
+        self.params.controller = int(kind)
+        self._check(lib().phipm_set_params(self.h, ctypes.byref(self.params)))
+
+    def mlp_forward(self, w, X, stream=None):
+        import torch
+        Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        self._check(lib().phipm_mlp_forward(self.h, w.data_ptr(), X.data_ptr(), X.shape[0], Y.data_ptr(),
+                                            _stream_ptr(stream)))
+        return Y
+
+    def mlp_grad(self, w, X, T, stream=None):
+        import torch
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self._check(lib().phipm_mlp_grad(self.h, w.data_ptr(), X.data_ptr(), T.data_ptr(), X.shape[0],
+                                         g.data_ptr(), loss.data_ptr(), _stream_ptr(stream)))
+        return g, float(loss.item())
+
+    def mlp_train(self, w, m, v, X, T, iters: int, t0: int = 0, lr: float = 1e-3, stream=None):
+        losses = (ctypes.c_float * max(iters, 1))()
+        self._check(lib().phipm_mlp_train(self.h, w.data_ptr(), m.data_ptr(), v.data_ptr(), X.data_ptr(),
+                                          T.data_ptr(), X.shape[0], int(iters), int(t0), float(lr), losses,
+                                          _stream_ptr(stream)))
+        return [float(losses[i]) for i in range(iters)]
+
+    def batch(self, t_end: list, ops: list, bs: list, tol: list, symm: list, outs: list = None) -> "Batch":
+        """Marshal a batch once; Batch.run() then repeats phipm_solve_batched on it (the
+        library replays its captured launch graph while nothing baked into it changes)."""
+        return Batch(self, t_end, ops, bs, tol, symm, outs)
+
     def solve_batched(self, t_end: list, ops: list, bs: list, tol: list, symm: list, outs: list = None,
                       stream=None, check: bool = True):
         """count independent problems in one persistent launch.  Returns (us, stats list, statuses)."""
@@ -261,6 +339,40 @@ class Phipm:
         if check:
             self._check(st)
         return outs, [s.as_dict() for s in ST], list(PS)
+
+
+class Batch:
+    """Prepared arguments of phipm_solve_batched (pointers of the given tensors, which
+    the caller keeps alive and in place)."""
+
+    def __init__(self, solver: Phipm, t_end, ops, bs, tol, symm, outs=None):
+        import torch
+        cnt = len(ops)
+        self.solver, self.count, self.ops, self.bs = solver, cnt, ops, bs
+        self.outs = outs if outs is not None else [torch.empty(A.n, dtype=torch.float64, device="cuda") for A in ops]
+        self.T = (c_double * cnt)(*[float(x) for x in t_end])
+        self.A = (OperatorC * cnt)(*[A.c for A in ops])
+        self.P = (c_int32 * cnt)(*[len(b) - 1 for b in bs])
+        self._rows = [(c_void_p * len(b))(*[x.data_ptr() for x in b]) for b in bs]
+        self.B = (ctypes.POINTER(c_void_p) * cnt)(*[ctypes.cast(r, ctypes.POINTER(c_void_p)) for r in self._rows])
+        self.TOL = (c_double * cnt)(*[float(x) for x in tol])
+        self.SY = (c_int32 * cnt)(*[int(x) for x in symm])
+        self.U = (c_void_p * cnt)(*[u.data_ptr() for u in self.outs])
+        self.ST = (StatsC * cnt)()
+        self.PS = (c_int32 * cnt)()
+
+    def run(self, stream=None, check: bool = True) -> int:
+        st = lib().phipm_solve_batched(self.solver.h, self.count, self.T, self.A, self.P, self.B, self.TOL, self.SY,
+                                       self.U, self.ST, self.PS, _stream_ptr(stream))
+        if check:
+            self.solver._check(st)
+        return st
+
+    def stats(self) -> list:
+        return [s.as_dict() for s in self.ST]
+
+    def statuses(self) -> list:
+        return list(self.PS)
 
 
 def solve_noalloc(t_end: float, A: DeviceOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,

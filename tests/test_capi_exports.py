@@ -35,7 +35,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     import os
     import subprocess
     structs = {"phipm_csr": pm.CsrC, "phipm_stencil": pm.StencilC, "phipm_operator": pm.OperatorC,
-               "phipm_stats": pm.StatsC, "phipm_params": pm.ParamsC}
+               "phipm_stats": pm.StatsC, "phipm_params": pm.ParamsC, "phipm_trace_record": pm.TraceRecordC}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "phipm.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
