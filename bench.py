@@ -337,7 +337,7 @@ def run_batched(args, world, rank, local):
     if spec.get("learned"):
         from paper_0907_4631_gb300 import learned as L
         t0 = time.perf_counter()
-        tr = L.training_problems(count=384, seed0=7000)
+        tr = L.training_problems(count=768, seed0=7000)
         X, T = L.examples_from_traces(L.collect_traces(solver, tr))
         blob, losses = L.train(solver, X, T, iters=3000, lr=3e-3)
         solver.set_controller_weights(blob)

@@ -190,6 +190,7 @@ typedef struct {
   double omega;       /* t_end eps / (tau Tol), Eq. (taunew)                             */
   double norm_a;      /* ||A||_inf                                                       */
   double tol;
+  double m_new;       /* unrounded, unrestricted m_new of Eq. (3) from this attempt      */
   int32_t source;     /* 0: tau, m from Algorithms 3-4; 1: proposed by the learned controller */
   int32_t rejects_prev; /* rejected attempts in the previous step                        */
 } phipm_trace_record;
@@ -206,18 +207,17 @@ phipm_status phipm_trace_read(phipm_handle* h, phipm_trace_record* out, int64_t 
  * W2[64x64], b2[64], W3[2x64], b3[2] (row-major).  A controller blob appends
  * x_mean[8], x_std[8], y_mean[2], y_std[2].
  *
- * Inputs (before normalisation), at the start of each step:
+ * Inputs (before normalisation), at the start of a step:
  *   log10(||A||_inf t_end), log10(Tol), p, log10(tau_start ||A||_inf),
  *   m_start / 64, log10(omega of the previous accepted attempt), rejected
  *   attempts in the previous step, log10(n),
  * where tau_start, m_start are the values Algorithm 3 carries into the step.
  * Outputs: log2(tau / tau_start) and m / 64 of the proposal.  With
- * params.controller = 1 and a blob installed, the first attempt of each of the
- * first 48 steps of a solve uses the proposal (tau ratio clamped to [1/32, 8] and
- * to the remaining interval, m to [1, m_max]); the error estimate still accepts
- * or rejects it, after a rejection the paper's controller takes over for the rest
- * of the step, and from step 48 on it runs alone (so a poor network costs a
- * bounded number of steps). */
+ * params.controller = 1 and a blob installed, the first attempt of the first
+ * step uses the proposal in place of Eq. (tau_0) and m_init (tau ratio clamped
+ * to [1/32, 8] and to the interval, m to [1, m_max]); the error estimate still
+ * accepts or rejects it, and the paper's controller handles every later attempt
+ * and step, whose proposals already rest on a measured error estimate. */
 #define PHIPM_MLP_PARAMS 4866
 #define PHIPM_CONTROLLER_FLOATS (PHIPM_MLP_PARAMS + 20)
 phipm_status phipm_set_controller_weights(phipm_handle* h, const float* blob, size_t count);

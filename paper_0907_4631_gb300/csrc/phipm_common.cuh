@@ -39,7 +39,7 @@ struct DevOp {
 // One attempt record; the same layout as phipm_trace_record in include/phipm.h.
 struct TraceRec {
   int problem, step, attempt, accepted, m_req, m_used, p, n;
-  double t, t_end, tau, eps, omega, norm_a, tol;
+  double t, t_end, tau, eps, omega, norm_a, tol, m_new;
   int source, rejects_prev;
 };
 

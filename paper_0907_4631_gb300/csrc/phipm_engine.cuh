@@ -11,19 +11,13 @@
 // FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
 #define PM_DRED 512                    // partials of one dot pass: PM_WARPS warps x PM_DSEG segments
-// The learned controller proposes (tau, m) for the first PM_LEARNED_STEPS steps of a
-// solve only; afterwards the paper's controller runs alone.  A network that keeps
-// proposing steps smaller than it needs to (or m too small) can therefore cost at most
-// that many steps before the paper's controller, whose tau grows geometrically when
-// omega is small (Eq. taunew), takes over.
-#define PM_LEARNED_STEPS 48
 
 // Scalar state of one problem.  Thread 0 writes it, every thread reads it after
 // the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
 // would cost a warp-wide FP64 instruction per warp on a pipe of about 2 FMA/clk/SM.
 struct PmScal {
   double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
-  double fnorm, last_tau, omega, last_omega;
+  double fnorm, last_tau, omega, last_omega, m_new;
   double tl[PM_MAXP + 1];
   df32 inv2;
   float invf;
@@ -811,8 +805,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       ctl_reset(ctl);
     }
     __syncthreads();
-    if (prm.mlp != nullptr && c.steps < PM_LEARNED_STEPS && tid < 32) {
-      // learned controller (a11): propose (tau, m) for the first attempt of this step
+    if (prm.mlp != nullptr && c.steps == 0 && tid < 32) {
+      // learned controller (a11): propose (tau, m) for the first attempt of the first
+      // step, in place of Eq. (tau_0) and m_init.  Later steps start from proposals of
+      // Algorithm 4 that rest on a measured error estimate; applied there too, small
+      // biases of the network compound from step to step (tau shrinking geometrically).
       const float* blob = prm.mlp;
       if (tid == 0) {
         const double raw[MLP_IN] = {log10(c.normA * c.t_end), log10(c.tol), (double)p, log10(c.tau * c.normA),
@@ -847,6 +844,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         c.tau_used = c.tau;
         c.m_req = c.m;
         c.m_used = c.m;
+        c.m_new = NAN;
         c.eps = 0.0;
         c.hlast = 0.0;
         c.sq = 0;
@@ -1001,6 +999,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         }
         if (!isfinite(c.eps)) {
           c.omega = c.eps;
+          c.m_new = NAN;
           c.nonfinite += 1;
           c.rejects += 1;
           c.outcome = PM_ATT_RETRY;
@@ -1043,6 +1042,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           }
           ctl.kap = kap; ctl.kf = kf;
           const double m_new_real = (omega > 0.0) ? m + log(omega / prm.gamma) / log(kap) : -INFINITY;   // Eq. (3)
+          c.m_new = m_new_real;
           int m_new;
           if (isfinite(m_new_real)) m_new = (int)fmin(fmax(ceil(m_new_real), 1.0), (double)m_max);
           else m_new = (m_new_real < 0.0) ? 1 : m_max;
@@ -1122,6 +1122,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             tr.omega = c.omega;
             tr.norm_a = c.normA;
             tr.tol = c.tol;
+            tr.m_new = c.m_new;
             tr.source = c.source;
             tr.rejects_prev = c.prev_rejects;
             c.trace_idx = (long long)idx;

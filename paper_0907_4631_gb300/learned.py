@@ -4,18 +4,21 @@ Flow (every numerical step of training and solving runs in libphipm's kernels;
 this module builds arrays and calls the library):
   1. solve a family of training problems with the paper's controller and
      attempt traces enabled (phipm_trace_enable);
-  2. turn each accepted step into one example: the features the solver
-     computes at the start of a step, and a hindsight label (tau*, m*), given
-     as log2(tau* / tau the step started with) and m* / 64:
-       - a step with rejected attempts: the accepted (tau, m), which the error
-         estimate has shown to be acceptable;
-       - a step accepted at once: the (tau, m) that the paper's controller
-         proposes right after it (Eq. taunew and the m update of Algorithm 4,
-         from the accepted attempt's error), its estimate of the largest
-         acceptable step.  The accepted tau itself would understate it, and
-         a network trained on it learns to shrink every step.
-     Such a step gives no example when it is the last one of its solve or
-     when the follow-up proposal was cut to the end of the interval;
+  2. turn each solve into one example: the features the solver computes at
+     the start of the first step (where Algorithm 3 starts from the heuristic
+     tau of Eq. (tau_0) and m_init) and a hindsight label (tau*, m*), given as
+     log2(tau* / tau_0) and m* / 64:
+       - first step with rejected attempts: the accepted tau, and the m of
+         Eq. (3) evaluated on the accepted attempt's error (the smallest m the
+         error model expects to meet the tolerance at that tau, at most
+         halving the accepted m, which the controller reached by growing m
+         in steps of 4/3 and usually overshot);
+       - first step accepted at once: the (tau, m) the paper's controller
+         proposes right after it (its estimate from a measured error), unless
+         that proposal was cut to the end of the interval;
+     The proposal is not applied to later steps: their start values already
+     rest on a measured error estimate, and small biases of a network
+     applied at every step compound (tau shrinking geometrically);
   3. standardise, train the 8-64-64-2 GELU network with phipm_mlp_train
      (full-batch Adam, mean squared error);
   4. install the blob (weights + standardisation) with
@@ -26,6 +29,7 @@ proposal block):
   log10(||A||_inf t_end), log10(Tol), p, log10(tau_start ||A||_inf), m_start / 64,
   log10(omega of the previous accepted attempt, floored at 1e-6; 1 before the
   first step), rejected attempts in the previous step, log10(n).
+At the first step the last three but one are constants (m_init / 64, 0, 0).
 """
 from __future__ import annotations
 
@@ -41,17 +45,18 @@ N_FEATURES = 8
 # --------------------------------------------------------------------------------------
 # training problems: seeded variants of the three single-problem configurations
 # --------------------------------------------------------------------------------------
-def training_problems(count: int = 384, seed0: int = 7000) -> list:
+def training_problems(count: int = 768, seed0: int = 7000) -> list:
     """Variants of the 2D Laplacian (config 1), the convection-diffusion family of
     config 2 (velocities spanning Peclet numbers 1..1e3) and the 3D Laplacian of
-    config 3, at sizes a single CTA solves quickly."""
+    config 3.  Grid sides are drawn log-uniformly up to 160 (2D Laplacian), 256
+    (convection-diffusion) and 40 (3D), so that n spans 256..65536."""
     probs = []
     for i in range(count):
         s = seed0 + i
         kind = i % 3
         u = wl.uniform(s, 1, 6)
         if kind == 0:
-            N = int(16 + u[0] * 48)
+            N = int(16 * 10 ** u[0])
             p = int(u[1] * 5) % 5
             t_end = 0.01 * 10 ** (2 * u[2] - 1)
             tol = 10 ** (-10 + 5 * u[3])
@@ -59,7 +64,7 @@ def training_problems(count: int = 384, seed0: int = 7000) -> list:
             b = [wl.normal(s, 100 + k, st.n) for k in range(p + 1)]
             probs.append(wl.Problem(f"tr_lap2_{i}", wl.stencil_to_csr(st), b, t_end, tol, 1, meta=dict(seed=s)))
         elif kind == 1:
-            N = int(16 + u[0] * 80)
+            N = int(16 * 16 ** u[0])
             p = 1 + int(u[1] * 4) % 4
             t_end = 1e-3 * 10 ** (2 * u[2] - 1)
             tol = 10 ** (-10 + 4 * u[3])
@@ -69,7 +74,7 @@ def training_problems(count: int = 384, seed0: int = 7000) -> list:
             b = [wl.normal(s, 100 + k, st.n) for k in range(p + 1)]
             probs.append(wl.Problem(f"tr_cd_{i}", wl.stencil_to_csr(st), b, t_end, tol, 0, meta=dict(seed=s)))
         else:
-            N = int(8 + u[0] * 14)
+            N = int(8 * 5 ** u[0])
             p = int(u[1] * 4) % 4
             t_end = 1e-4 * 10 ** (2 * u[2] - 1)
             tol = 10 ** (-9 + 4 * u[3])
@@ -83,42 +88,40 @@ def training_problems(count: int = 384, seed0: int = 7000) -> list:
 # traces -> examples
 # --------------------------------------------------------------------------------------
 def examples_from_traces(records: list) -> tuple:
-    """(X_raw [k x 8], T_raw [k x 2]) from attempt records of one or more solves."""
+    """(X_raw [k x 8], T_raw [k x 2]) from attempt records of one or more solves:
+    one example per solve, from its first step (the step the learned proposal
+    replaces)."""
     by_prob: dict = {}
     for r in records:
-        by_prob.setdefault(r["problem"], []).append(r)
+        if r["step"] <= 1:
+            by_prob.setdefault(r["problem"], []).append(r)
     X, T = [], []
     for prob, recs in by_prob.items():
-        steps: dict = {}
-        for r in recs:
-            steps.setdefault(r["step"], []).append(r)
-        omega_prev = 1.0
-        order = sorted(steps)
-        for k in order:
-            att = sorted(steps[k], key=lambda r: r["attempt"])
-            acc = [r for r in att if r["accepted"]]
-            if not acc:
-                continue
-            r0, ra = att[0], acc[-1]
-            nxt = steps.get(k + 1)
-            rn = min(nxt, key=lambda r: r["attempt"]) if nxt else None
-            na = r0["norm_a"]
-            if len(att) > 1:
-                label = (ra["tau"], ra["m_used"])
-            elif (rn is not None and rn["attempt"] == 0 and rn["tau"] > 0
-                  and rn["t"] + rn["tau"] < rn["t_end"] * (1.0 - 1e-12)):
-                label = (rn["tau"], rn["m_req"])
-            else:
-                label = None
-            if label is not None and r0["attempt"] == 0 and na > 0 and r0["tau"] > 0:
-                x = [math.log10(na * r0["t_end"]), math.log10(r0["tol"]), float(r0["p"]),
-                     math.log10(r0["tau"] * na), r0["m_req"] / 64.0, math.log10(max(omega_prev, 1e-6)),
-                     float(r0["rejects_prev"]), math.log10(r0["n"])]
-                t = [math.log2(label[0] / r0["tau"]), label[1] / 64.0]
-                if all(math.isfinite(v) for v in x + t):
-                    X.append(x)
-                    T.append(t)
-            omega_prev = ra["omega"] if math.isfinite(ra["omega"]) else 1.0
+        first = sorted((r for r in recs if r["step"] == 0), key=lambda r: r["attempt"])
+        nxt = sorted((r for r in recs if r["step"] == 1), key=lambda r: r["attempt"])
+        acc = [r for r in first if r["accepted"]]
+        if not first or not acc or first[0]["attempt"] != 0:
+            continue
+        r0, ra = first[0], acc[-1]
+        if len(first) > 1:
+            # accepted tau; m_new of Eq. (3) from the accepted attempt (at most halving m)
+            mn = ra["m_new"]
+            m_lab = ra["m_used"] if not math.isfinite(mn) else min(ra["m_used"], max(math.ceil(mn),
+                                                                                      ra["m_used"] // 2, 1))
+            label = (ra["tau"], m_lab)
+        elif nxt and nxt[0]["attempt"] == 0 and nxt[0]["t"] + nxt[0]["tau"] < nxt[0]["t_end"] * (1.0 - 1e-12):
+            label = (nxt[0]["tau"], nxt[0]["m_req"])
+        else:
+            continue
+        na = r0["norm_a"]
+        if not (na > 0 and r0["tau"] > 0 and label[0] > 0):
+            continue
+        x = [math.log10(na * r0["t_end"]), math.log10(r0["tol"]), float(r0["p"]), math.log10(r0["tau"] * na),
+             r0["m_req"] / 64.0, 0.0, float(r0["rejects_prev"]), math.log10(r0["n"])]
+        t = [math.log2(label[0] / r0["tau"]), label[1] / 64.0]
+        if all(math.isfinite(v) for v in x + t):
+            X.append(x)
+            T.append(t)
     return np.asarray(X, dtype=np.float64).reshape(-1, N_FEATURES), np.asarray(T, dtype=np.float64).reshape(-1, 2)
 
 

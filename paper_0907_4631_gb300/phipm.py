@@ -50,7 +50,8 @@ class TraceRecordC(ctypes.Structure):
     _fields_ = [("problem", c_int32), ("step", c_int32), ("attempt", c_int32), ("accepted", c_int32),
                 ("m_req", c_int32), ("m_used", c_int32), ("p", c_int32), ("n", c_int32),
                 ("t", c_double), ("t_end", c_double), ("tau", c_double), ("eps", c_double), ("omega", c_double),
-                ("norm_a", c_double), ("tol", c_double), ("source", c_int32), ("rejects_prev", c_int32)]
+                ("norm_a", c_double), ("tol", c_double), ("m_new", c_double), ("source", c_int32),
+                ("rejects_prev", c_int32)]
 
 
 class ParamsC(ctypes.Structure):
