@@ -20,10 +20,10 @@
 // ------------------------------------------------------------------------------------
 template <class S>
 __global__ void __launch_bounds__(PM_THREADS, 1)
-k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned* bar, int* err) {
+k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned long long* bar, int* err) {
   extern __shared__ __align__(16) unsigned char pm_smem[];
   PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
-  GridTeam team{bar, err, prm.timeout_cycles};
+  GridTeam team{bar, err, prm.timeout_cycles, 0ull};
   phipm_device<GridTeam, S>(team, P, prm, *res, s, w);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int e = *((volatile int*)err);
@@ -549,7 +549,7 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
     }
     PmWork w{(double*)h->partials.p, (double*)h->expm.p};
-    unsigned* bar = (unsigned*)h->sync.p;
+    unsigned long long* bar = (unsigned long long*)h->sync.p;
     int* err = (int*)((char*)h->sync.p + 1024);
     if ((e = cudaMemsetAsync(h->sync.p, 0, 2048, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
     if ((e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess) return cuda_fail(h, e, "memset");

@@ -85,38 +85,41 @@ struct DevResult {
 // ------------------------------------------------------------------------------------
 // bounded waits
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned pm_ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// Barrier over the G CTAs of a cooperative launch on one 64-bit arrival counter
+// that the host zeroes before the launch and that only grows: the k-th barrier is
+// passed once it reaches k G.  Each CTA counts its own barriers (gen, thread 0),
+// so arriving takes one acquire-release atomic and waiting one acquire load per
+// poll, with no generation word and no separate fences.  The spin is bounded by
+// timeout cycles; on expiry the error word is set and every later barrier returns
+// at once (err is checked every 16 polls).
+__device__ __forceinline__ unsigned long long pm_atom_add_acq_rel(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long pm_ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-
-// Barrier over G CTAs of a cooperative launch.  bar[0] = arrival count,
-// bar[32] = generation.  The spin is bounded by timeout cycles; on expiry the
-// error word is set and every later barrier returns at once.
-__device__ __forceinline__ bool pm_grid_barrier(unsigned* bar, int G, int* err, long long timeout) {
+__device__ __forceinline__ bool pm_grid_barrier(unsigned long long* cnt, int G, int* err, long long timeout,
+                                                unsigned long long& gen) {
   __syncthreads();
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
     s_fail = 0;
-    unsigned* count = bar;
-    unsigned* gen = bar + 32;
-    unsigned g = pm_ld_acquire(gen);
-    __threadfence();
-    unsigned prev = atomicAdd(count, 1u);
-    if (prev == (unsigned)G - 1) {
-      *count = 0;
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long t0 = clock64();
-      while (pm_ld_acquire(gen) == g) {
-        if (*((volatile int*)err) != 0) { s_fail = 1; break; }
-        if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_fail = 1; break; }
-        __nanosleep(64);
+    gen += 1;
+    const unsigned long long target = gen * (unsigned long long)G;
+    const unsigned long long prev = pm_atom_add_acq_rel(cnt, 1ull);
+    if (prev + 1 < target) {
+      const long long t0 = clock64();
+      for (unsigned it = 1; pm_ld_acquire64(cnt) < target; ++it) {
+        if ((it & 15u) == 0) {
+          if (*((volatile int*)err) != 0) { s_fail = 1; break; }
+          if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_fail = 1; break; }
+        }
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return s_fail == 0;
@@ -124,12 +127,13 @@ __device__ __forceinline__ bool pm_grid_barrier(unsigned* bar, int G, int* err, 
 
 // A team is the set of CTAs that work on one problem.
 struct GridTeam {
-  unsigned* bar;
+  unsigned long long* bar;               // arrival counter, zero at launch
   int* err;
   long long timeout;
+  mutable unsigned long long gen = 0;    // barriers passed (used by thread 0)
   __device__ int rank() const { return blockIdx.x; }
   __device__ int size() const { return gridDim.x; }
-  __device__ bool sync() const { return pm_grid_barrier(bar, gridDim.x, err, timeout); }
+  __device__ bool sync() const { return pm_grid_barrier(bar, gridDim.x, err, timeout, gen); }
   static constexpr bool multi = true;
 };
 

@@ -10,7 +10,7 @@
 
 // FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
-#define PM_DRED 512                    // partials of one dot pass: PM_WARPS warps x PM_DSEG segments
+#define PM_DRED (PM_WARPS * (PM_NSLOT + 2))   // partials of a dot pass (vector x warp) or of a team fold
 
 // Scalar state of one problem.  Thread 0 writes it, every thread reads it after
 // the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
@@ -42,6 +42,9 @@ struct PmShared {
   df32 ucd[PM_NSLOT];
   double dred[PM_DRED];                // per-segment partial dots of one pass
   double wy[PM_WARPS][PM_NA];          // per-warp column of the exponential's solve
+  double lu[PM_NA2];                   // LU factors of the Pade denominator (every CTA its own)
+  double rdiag[PM_NA];                 // reciprocals of U's diagonal
+  int piv[PM_NA];
   float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
 };
@@ -56,6 +59,41 @@ struct PmWork {
 // ------------------------------------------------------------------------------------
 // team reductions of K values held in s.coef[0..K) by each CTA
 // ------------------------------------------------------------------------------------
+// After the team barrier every CTA folds the G partial rows P[g][0..K) into
+// s.coef[0..K).  The G x K loads are cut into units (k, block of CTAs) so that each
+// thread has up to PM_RB independent L2 loads in flight (a lane-strided loop leaves
+// one load per lane outstanding and pays the L2 latency G / 32 times per k); units
+// are folded in a fixed order, so every CTA gets bit-identical results.
+#define PM_RB 16
+template <bool MAX>
+__device__ __forceinline__ void team_fold(PmShared& s, const double* P, int G, int K) {
+  if (K <= 0) { __syncthreads(); return; }
+  int nb = (G + PM_RB - 1) / PM_RB;
+  nb = max(1, min(nb, PM_DRED / K));
+  const int gpb = (G + nb - 1) / nb;          // CTAs per unit
+  const double id = MAX ? -INFINITY : 0.0;
+  for (int u = threadIdx.x; u < K * nb; u += blockDim.x) {
+    const int k = u / nb, b = u - k * nb;
+    const int g0 = b * gpb, g1 = min(G, g0 + gpb);
+    double a = id;
+    for (int g = g0; g < g1; g += PM_RB) {
+      double v[PM_RB];
+#pragma unroll
+      for (int q = 0; q < PM_RB; ++q) v[q] = (g + q < g1) ? __ldcg(&P[(size_t)(g + q) * PM_PSTRIDE + k]) : id;
+#pragma unroll
+      for (int q = 0; q < PM_RB; ++q) a = MAX ? fmax(a, v[q]) : a + v[q];
+    }
+    s.dred[u] = a;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double a = s.dred[k * nb];
+    for (int b = 1; b < nb; ++b) a = MAX ? fmax(a, s.dred[k * nb + b]) : a + s.dred[k * nb + b];
+    s.coef[k] = a;
+  }
+  __syncthreads();
+}
+
 template <class Team>
 __device__ bool team_sum(const Team& team, PmShared& s, int K, const PmWork& w, int& parity) {
   if (!Team::multi) { __syncthreads(); return true; }
@@ -64,14 +102,7 @@ __device__ bool team_sum(const Team& team, PmShared& s, int K, const PmWork& w, 
   parity ^= 1;
   for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
   if (!team.sync()) return false;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < K; k += PM_WARPS) {
-    double a = 0.0;
-    for (int g = lane; g < G; g += 32) a += __ldcg(&P[(size_t)g * PM_PSTRIDE + k]);
-    a = pm_warp_sum(a);
-    if (lane == 0) s.coef[k] = a;
-  }
-  __syncthreads();
+  team_fold<false>(s, P, G, K);
   return true;
 }
 
@@ -83,14 +114,7 @@ __device__ bool team_max(const Team& team, PmShared& s, int K, const PmWork& w, 
   parity ^= 1;
   for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
   if (!team.sync()) return false;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < K; k += PM_WARPS) {
-    double a = -1.0;
-    for (int g = lane; g < G; g += 32) a = fmax(a, __ldcg(&P[(size_t)g * PM_PSTRIDE + k]));
-    a = pm_warp_max(a);
-    if (lane == 0) s.coef[k] = a;
-  }
-  __syncthreads();
+  team_fold<true>(s, P, G, K);
   return true;
 }
 
@@ -134,18 +158,28 @@ __device__ __forceinline__ df32 ld_cg(const df32* p) {
   r.lo = v.y;
   return r;
 }
+// x(i) for the SpMV.  With CG (grid team) rows outside this CTA's [lo, hi), written
+// by other CTAs during the launch, are read through L2; the CTA's own rows, written
+// only by itself (row blocks are 64-aligned, so no cache line is shared between
+// CTAs), use the L1-cached path, where stencil neighbours reuse each other's lines.
 template <class S, bool CG> struct VecLoad {
   const S* p;
+  int lo, hi;
   __device__ __forceinline__ S operator()(int i) const {
-    if constexpr (CG) return ld_cg(p + i);
-    else return p[i];
+    if constexpr (CG) {
+      if ((unsigned)(i - lo) >= (unsigned)(hi - lo)) return ld_cg(p + i);
+    }
+    return p[i];
   }
 };
 template <class S, bool CG> struct DLoadAs {      // FP64 vector read as S
   const double* p;
+  int lo, hi;
   __device__ __forceinline__ S operator()(int i) const {
-    if constexpr (CG) return Elem<S>::from_d(__ldcg(p + i));
-    else return Elem<S>::from_d(p[i]);
+    if constexpr (CG) {
+      if ((unsigned)(i - lo) >= (unsigned)(hi - lo)) return Elem<S>::from_d(__ldcg(p + i));
+    }
+    return Elem<S>::from_d(p[i]);
   }
 };
 
@@ -226,6 +260,81 @@ __device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
 // ------------------------------------------------------------------------------------
 // Gram-Schmidt passes over this CTA's rows [lo, hi)
 // ------------------------------------------------------------------------------------
+// Row-owner form of dots_cta for one or two products (Lanczos): each thread owns
+// four consecutive rows per tile of 4 x blockDim rows (16-byte accesses; lo is a
+// multiple of 64 and vectors are 256-byte aligned), loads its quad of y once per
+// tile together with the (at most two) vectors' quads; each warp reduces its
+// partial per vector and accumulates it over the tiles in s.dred[i][warp]; d_i
+// then sums the warps in order (deterministic).  With more vectors the per-vector
+// warp reductions serialise the loads, and the run-per-warp form below is faster.
+template <class S>
+__device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo, int hi,
+                         bool with_norm, PmShared& s) {
+  typedef Elem<S> E;
+  typedef typename E::Acc Acc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nvec = nv + (with_norm ? 1 : 0);
+  if (hi <= lo) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    __syncthreads();
+    return;
+  }
+  double* red = s.dred;                      // [nvec][PM_WARPS]
+  const int span = 4 * blockDim.x;
+  for (int base = lo; base < hi; base += span) {
+    const int r = base + 4 * threadIdx.x;
+    const int nr = max(0, min(4, hi - r));   // rows of this thread in the tile
+    Quad<S> yq;
+    if (nr == 4) {
+      yq.load(y + r);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) yq.x[k] = (k < nr) ? y[r + k] : E::from_d(0.0);
+    }
+    constexpr int NG = 2;                      // vectors per group
+    for (int i0 = 0; i0 < nvec; i0 += NG) {
+      double d[NG];
+      Quad<S> vq[NG];
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        const int i = i0 + u;
+        if (i < nvec) {
+          const S* v = (i < nv) ? V + (size_t)i * ld : y;
+          if (nr == 4) {
+            vq[u].load(v + r);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) vq[u].x[k] = (k < nr) ? v[r + k] : E::from_d(0.0);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        Acc acc = E::zero();
+        if (i0 + u < nvec) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) E::dot(acc, vq[u].x[k], yq.x[k]);
+        }
+        d[u] = pm_warp_sum(E::val(acc));
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < NG; ++u) {
+          const int i = i0 + u;
+          if (i < nvec) red[i * PM_WARPS + warp] = (base == lo ? 0.0 : red[i * PM_WARPS + warp]) + d[u];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < PM_WARPS; ++w) t += red[i * PM_WARPS + w];
+    s.coef[i] = t;
+  }
+  __syncthreads();
+}
+
 // d_i = sum_r V[i][r] y[r], i < nv, into s.coef[0..nv); with_norm adds sum y^2
 // as s.coef[nv].  The nvec x rows products, taken vector after vector, are cut
 // into PM_WARPS equal contiguous runs, one per warp, so every warp streams a long
@@ -276,6 +385,10 @@ __device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S*
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + (with_norm ? 1 : 0);
+  if (nvec <= 2) {           // one or two products: one pass over rows, y loaded once
+    dots_rows<S>(V, ld, nv, y, lo, hi, with_norm, s);
+    return;
+  }
   const long long total = (long long)nvec * rows;
   if (total == 0) {
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
@@ -403,27 +516,53 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
 #define PM_EXPM_MATS 13
 #define PM_EXPM_DOUBLES (PM_EXPM_MATS * PM_NA2 + 2 * PM_NA + PM_NA)
 
-// C = A * B on the elements [e0, e1) of the N x N result (row-major, stride PM_NA);
-// operands written by other CTAs are read through L2.
+template <bool CG>
+__device__ __forceinline__ double ldx(const double* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+// C = A * B on the elements [e0, e1) of the N x N result (row-major, stride PM_NA).
+// Grid team (MULTI): a CTA owns a few elements; one warp per element with the lanes
+// splitting k, so all loads of an element are in flight at once (operands written
+// by other CTAs: through L2).  One CTA: one thread per element, operands written by
+// this CTA (L1-cached).
+static_assert(3 * 32 >= PM_NA, "three k-slices per lane cover the augmented matrix");
+template <bool MULTI>
 __device__ __forceinline__ void mm_elems(double* C, const double* A, const double* B, int N, int e0, int e1) {
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int i = e / N, j = e - i * N;
-    const double* a = A + i * PM_NA;
-    double c0 = 0.0, c1 = 0.0;
-    int k = 0;
-    for (; k + 1 < N; k += 2) {
-      c0 = fma(__ldcg(&a[k]), __ldcg(&B[k * PM_NA + j]), c0);
-      c1 = fma(__ldcg(&a[k + 1]), __ldcg(&B[(k + 1) * PM_NA + j]), c1);
+  if constexpr (MULTI) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = e0 + warp; e < e1; e += PM_WARPS) {
+      const int i = e / N, j = e - i * N;
+      double c = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int k = lane + 32 * q;
+        if (k < N) c = fma(__ldcg(&A[i * PM_NA + k]), __ldcg(&B[k * PM_NA + j]), c);
+      }
+      c = pm_warp_sum(c);
+      if (lane == 0) C[i * PM_NA + j] = c;
     }
-    if (k < N) c0 = fma(__ldcg(&a[k]), __ldcg(&B[k * PM_NA + j]), c0);
-    C[i * PM_NA + j] = c0 + c1;
+  } else {
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = e / N, j = e - i * N;
+      const double* a = A + i * PM_NA;
+      double c0 = 0.0, c1 = 0.0;
+      int k = 0;
+      for (; k + 1 < N; k += 2) {
+        c0 = fma(a[k], B[k * PM_NA + j], c0);
+        c1 = fma(a[k + 1], B[(k + 1) * PM_NA + j], c1);
+      }
+      if (k < N) c0 = fma(a[k], B[k * PM_NA + j], c0);
+      C[i * PM_NA + j] = c0 + c1;
+    }
   }
 }
 
 // exp(H_hat) with H_hat = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]] (Eq. hathm,
 // size N = m+p+1), degree-13 Pade approximant (even/odd split) with sq
-// squarings (Sec. 3.1).  Products are split over the team by elements; the LU
-// factorisation of the denominator runs on rank 0; the right-hand sides are
+// squarings (Sec. 3.1).  Products are split over the team by elements; every CTA
+// factorises the denominator in its own shared memory; the right-hand sides are
 // split by columns; only columns ca and cb of the last square are formed.
 // On return every CTA holds the top m entries of those columns in s.phi0/phi1.
 template <class Team>
@@ -445,7 +584,6 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
   double* R = ws + 11 * PM_NA2;
   double* R2 = ws + 12 * PM_NA2;
   double* out = ws + PM_EXPM_MATS * PM_NA2;
-  int* piv = reinterpret_cast<int*>(out + 2 * PM_NA);
   int e0, e1;
   split_range(NN, rk, G, e0, e1);
   const double sc = ldexp(1.0, -sq);
@@ -458,11 +596,11 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     X[i * PM_NA + j] = v * sc;
   }
   if (!team.sync()) return false;
-  mm_elems(X2, X, X, N, e0, e1);
+  mm_elems<Team::multi>(X2, X, X, N, e0, e1);
   if (!team.sync()) return false;
-  mm_elems(X4, X2, X2, N, e0, e1);
+  mm_elems<Team::multi>(X4, X2, X2, N, e0, e1);
   if (!team.sync()) return false;
-  mm_elems(X6, X4, X2, N, e0, e1);
+  mm_elems<Team::multi>(X6, X4, X2, N, e0, e1);
   __syncthreads();
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
@@ -470,8 +608,8 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     T2[o] = bc[12] * X6[o] + bc[10] * X4[o] + bc[8] * X2[o];
   }
   if (!team.sync()) return false;
-  mm_elems(U, X6, T1, N, e0, e1);
-  mm_elems(Vm, X6, T2, N, e0, e1);
+  mm_elems<Team::multi>(U, X6, T1, N, e0, e1);
+  mm_elems<Team::multi>(Vm, X6, T2, N, e0, e1);
   __syncthreads();
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
@@ -480,7 +618,7 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     Vm[o] = Vm[o] + bc[6] * X6[o] + bc[4] * X4[o] + bc[2] * X2[o] + bc[0] * id;
   }
   if (!team.sync()) return false;
-  mm_elems(U2, X, U, N, e0, e1);     // odd part X * (...)
+  mm_elems<Team::multi>(U2, X, U, N, e0, e1);     // odd part X * (...)
   __syncthreads();
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int i = e / N, j = e - i * N, o = i * PM_NA + j;
@@ -488,16 +626,22 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     Q[o] = Vm[o] - U2[o];            // denominator
   }
   if (!team.sync()) return false;
-  // LU factorisation with partial pivoting of Q (rank 0, in place; every read of Q
-  // goes through L2 since other CTAs formed it)
-  if (rk == 0) {
+  // LU factorisation with partial pivoting of Q, by every CTA in its own shared
+  // memory (at most 73 x 73): no CTA waits for another, the factors are bit-identical
+  // in every CTA (same inputs, same order), and the solves below read them at shared-
+  // memory latency.  Q was formed by other CTAs: read through L2.
+  {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* L = s.lu;
+    for (int i = warp; i < N; i += PM_WARPS)
+      for (int j = lane; j < N; j += 32) L[i * PM_NA + j] = ldx<Team::multi>(&Q[i * PM_NA + j]);
+    __syncthreads();
     for (int k = 0; k < N; ++k) {
       if (warp == 0) {
         double best = -1.0;
         int bi = k;
         for (int i = k + lane; i < N; i += 32) {
-          const double a = fabs(__ldcg(&Q[i * PM_NA + k]));
+          const double a = fabs(L[i * PM_NA + k]);
           if (a > best) { best = a; bi = i; }
         }
 #pragma unroll
@@ -508,53 +652,53 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
         }
         if (bi != k)
           for (int j = lane; j < N; j += 32) {
-            const double t = __ldcg(&Q[k * PM_NA + j]);
-            Q[k * PM_NA + j] = __ldcg(&Q[bi * PM_NA + j]);
-            Q[bi * PM_NA + j] = t;
+            const double t = L[k * PM_NA + j];
+            L[k * PM_NA + j] = L[bi * PM_NA + j];
+            L[bi * PM_NA + j] = t;
           }
         __syncwarp();
-        const double pv = __ldcg(&Q[k * PM_NA + k]);
-        for (int i = k + 1 + lane; i < N; i += 32) Q[i * PM_NA + k] = __ldcg(&Q[i * PM_NA + k]) / pv;
-        if (lane == 0) piv[k] = bi;
-        __syncwarp();
+        const double rp = 1.0 / L[k * PM_NA + k];
+        for (int i = k + 1 + lane; i < N; i += 32) L[i * PM_NA + k] *= rp;
+        if (lane == 0) {
+          s.piv[k] = bi;
+          s.rdiag[k] = rp;
+        }
       }
       __syncthreads();
-      const int w = N - k - 1;
-      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-        const int i = k + 1 + e / w, j = k + 1 + e % w;
-        Q[i * PM_NA + j] = fma(-__ldcg(&Q[i * PM_NA + k]), __ldcg(&Q[k * PM_NA + j]), __ldcg(&Q[i * PM_NA + j]));
+      for (int i = k + 1 + warp; i < N; i += PM_WARPS) {
+        const double lik = L[i * PM_NA + k];
+        for (int j = k + 1 + lane; j < N; j += 32) L[i * PM_NA + j] = fma(-lik, L[k * PM_NA + j], L[i * PM_NA + j]);
       }
       __syncthreads();
     }
   }
-  if (!team.sync()) return false;
   // R = Q^{-1} P, one warp per column, columns split over the team
   {
     int c0, c1;
     split_range(N, rk, G, c0, c1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* L = s.lu;
     double* yv = s.wy[warp];
     for (int j = c0 + warp; j < c1; j += PM_WARPS) {
-      for (int i = lane; i < N; i += 32) yv[i] = __ldcg(&Pm[i * PM_NA + j]);
+      for (int i = lane; i < N; i += 32) yv[i] = ldx<Team::multi>(&Pm[i * PM_NA + j]);
       __syncwarp();
       if (lane == 0)
         for (int k = 0; k < N; ++k) {
-          const int pk = __ldcg(&piv[k]);
+          const int pk = s.piv[k];
           if (pk != k) { const double t = yv[k]; yv[k] = yv[pk]; yv[pk] = t; }
         }
       __syncwarp();
-      for (int i = 1; i < N; ++i) {          // unit lower triangular
-        double a = 0.0;
-        for (int k = lane; k < i; k += 32) a = fma(__ldcg(&Q[i * PM_NA + k]), yv[k], a);
-        a = pm_warp_sum(a);
-        if (lane == 0) yv[i] -= a;
+      // column-oriented substitutions: each step is one FMA per lane, no reduction
+      for (int k = 0; k + 1 < N; ++k) {      // unit lower triangular
+        const double yk = yv[k];
+        for (int i = k + 1 + lane; i < N; i += 32) yv[i] = fma(-L[i * PM_NA + k], yk, yv[i]);
         __syncwarp();
       }
-      for (int i = N - 1; i >= 0; --i) {     // upper triangular
-        double a = 0.0;
-        for (int k = i + 1 + lane; k < N; k += 32) a = fma(__ldcg(&Q[i * PM_NA + k]), yv[k], a);
-        a = pm_warp_sum(a);
-        if (lane == 0) yv[i] = (yv[i] - a) / __ldcg(&Q[i * PM_NA + i]);
+      for (int k = N - 1; k >= 0; --k) {     // upper triangular
+        const double yk = yv[k] * s.rdiag[k];
+        __syncwarp();
+        if (lane == 0) yv[k] = yk;
+        for (int i = lane; i < k; i += 32) yv[i] = fma(-L[i * PM_NA + k], yk, yv[i]);
         __syncwarp();
       }
       for (int i = lane; i < N; i += 32) R[i * PM_NA + j] = yv[i];
@@ -566,31 +710,36 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
   double* cur = R;
   double* oth = R2;
   for (int q = 0; q + 1 < sq; ++q) {
-    mm_elems(oth, cur, cur, N, e0, e1);
+    mm_elems<Team::multi>(oth, cur, cur, N, e0, e1);
     if (!team.sync()) return false;
     double* t = cur; cur = oth; oth = t;
   }
   {
     int r0, r1;
     split_range(2 * N, rk, G, r0, r1);
-    for (int e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = r0 + warp; e < r1; e += PM_WARPS) {     // one warp per entry, lanes split k
       const int which = e / N, i = e - which * N;
       const int col = which ? cb : ca;
       double v;
       if (sq == 0) {
-        v = __ldcg(&cur[i * PM_NA + col]);
+        v = ldx<Team::multi>(&cur[i * PM_NA + col]);
       } else {
         double c0 = 0.0;
-        for (int k = 0; k < N; ++k) c0 = fma(__ldcg(&cur[i * PM_NA + k]), __ldcg(&cur[k * PM_NA + col]), c0);
-        v = c0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int k = lane + 32 * q;
+          if (k < N) c0 = fma(ldx<Team::multi>(&cur[i * PM_NA + k]), ldx<Team::multi>(&cur[k * PM_NA + col]), c0);
+        }
+        v = pm_warp_sum(c0);
       }
-      out[which * PM_NA + i] = v;
+      if (lane == 0) out[which * PM_NA + i] = v;
     }
   }
   if (!team.sync()) return false;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    s.phi0[i] = __ldcg(&out[i]);
-    s.phi1[i] = __ldcg(&out[PM_NA + i]);
+    s.phi0[i] = ldx<Team::multi>(&out[i]);
+    s.phi1[i] = ldx<Team::multi>(&out[PM_NA + i]);
   }
   __syncthreads();
   return true;
@@ -771,7 +920,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       const double* xin = (j == 1) ? u : W + (size_t)(j - 2) * ld;
       double* wout = W + (size_t)(j - 1) * ld;
       double nrm = 0.0;
-      VecLoad<double, Team::multi> xl{xin};
+      VecLoad<double, Team::multi> xl{xin, lo, hi};
       for (int r = lo + tid; r < hi; r += nth) {
         double y = spmv_row<double>(P.A, r, xl);
         for (int l = 0; l <= p - j; ++l) y = fma(c.tl[l], P.b[j + l][r], y);
@@ -862,16 +1011,20 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             const S* yprev = Y + (size_t)((j + 1) & 1) * ld;
             const C sc = scal_inv<S>(c);   // 1/beta at j = 0, else 1/||y_{j-1}||
             if (j == 0) {
-              for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
-              DLoadAs<S, Team::multi> xl{wp};
-              for (int r = lo + tid; r < hi; r += nth) ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+              DLoadAs<S, Team::multi> xl{wp, lo, hi};
+              for (int r = lo + tid; r < hi; r += nth) {
+                V[r] = E::from_d(wp[r] * c.inv);
+                ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+              }
             } else if (j == j0) {
-              VecLoad<S, Team::multi> xl{V + (size_t)j * ld};   // v_j normalised at the end of the previous extension
+              VecLoad<S, Team::multi> xl{V + (size_t)j * ld, lo, hi};   // v_j normalised at the end of the previous extension
               for (int r = lo + tid; r < hi; r += nth) ycur[r] = spmv_row<S>(P.A, r, xl);
             } else {
-              for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
-              VecLoad<S, Team::multi> xl{yprev};
-              for (int r = lo + tid; r < hi; r += nth) ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+              VecLoad<S, Team::multi> xl{yprev, lo, hi};
+              for (int r = lo + tid; r < hi; r += nth) {
+                V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
+                ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+              }
             }
             matvecs += 1;
             kry_steps += 1;
