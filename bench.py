@@ -546,6 +546,7 @@ def main():
     ap.add_argument("--workload", default="convdiff2d_512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default team size (no phipm_autotune)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -579,6 +580,10 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    tune = None
+    if not args.no_autotune:     # untimed: picks the team size for this size class
+        tune = solver.autotune(pr.t_end, A, b, pr.tol, pr.symm, out=u)
+    team = solver.team_for(0 if hasattr(pr.op, "rowptr") else 1, pr.n)
     for _ in range(args.warmup):
         solver.solve(pr.t_end, A, b, pr.tol, pr.symm, out=u)
     torch.cuda.synchronize()
@@ -649,7 +654,7 @@ def main():
     kernel_ms = statistics.mean(kms)
     abytes = algorithmic_bytes(pr, stats, spec["precision"])
     achieved = abytes / (kernel_ms / 1e3) / 1e9
-    kernel_name = "k_solve_grid" if pr.n >= 16384 else "k_solve_queue"
+    kernel_name = "k_solve_grid" if team >= 2 else "k_solve_queue"
     traffic = traffic_from_profiles(kernel_name, args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
@@ -662,7 +667,8 @@ def main():
         "data": "synthetic (seeded counter-based generator; same inputs as the oracle)",
         "config": {"workload": args.workload, "n": pr.n, "nnz": int(pr.op.nnz if hasattr(pr.op, "rowptr") else pr.op.nnz()),
                    "p": pr.p, "t_end": pr.t_end, "tol": pr.tol, "l2": "flushed between timed solves (256 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "team": team, "autotune_ms": {str(t): round(ms, 3) for t, ms in tune} if tune else None},
         "solver_stats": {k: stats[k] for k in ("steps", "rejects", "matvecs", "expms", "krylov_steps", "gs_vectors")},
         "gpu_launches": args.steps * (2 if (spec["precision"] != "f64" and hasattr(pr.op, "rowptr")) else 1),
         "roofline": roofline,

@@ -260,6 +260,48 @@ phipm_status phipm_mlp_train(phipm_handle* h, float* w, float* m, float* v, cons
 phipm_status phipm_solve_noalloc(double t_end, const phipm_operator* A, int32_t p, const double* const* b,
                                  double tol, int32_t symm, double* u, phipm_stats* stats, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Team-size autotuner (the paper has no counterpart; a library service).
+ *
+ * A solve runs on a team of CTAs: one CTA (the whole problem in one SM's shared
+ * state) or a cooperative grid of G CTAs, each owning a 64-row-aligned block
+ * of every vector, with grid-wide reductions and barriers between phases.  The
+ * best G depends on n, the operator and the precision: more CTAs add memory
+ * parallelism and split the exponential, but every Krylov step pays two or
+ * three grid barriers.  Without tuning a solve uses one CTA below n = 16384 and
+ * every co-resident CTA from there on.
+ *
+ * phipm_autotune solves the given problem (arguments as phipm_solve; device
+ * buffers) with each candidate team size -- 1, 2, 4, 8, 16, 32 and 1/4, 1/2 and
+ * all of the co-resident grid, keeping only sizes that leave every CTA at least
+ * 64 rows -- timing the second of two solves per candidate, and records the
+ * fastest for the problem's size class (precision, operator kind, floor(log2 n)).
+ * Later phipm_solve / phipm_solve_host calls of that class use it.  u holds the
+ * last solve's result.  report (host, may be NULL) receives up to max_report
+ * (team, kernel_ms) pairs in the order tried; *n_report (may be NULL) their count.
+ * Errors are those of phipm_solve.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t team;        /* CTAs cooperating on the solve (1 = one CTA)  */
+  int32_t reserved;
+  double kernel_ms;    /* solver kernel time of the timed solve         */
+} phipm_tune_entry;
+phipm_status phipm_autotune(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
+                            const double* const* b, double tol, int32_t symm, double* u,
+                            phipm_tune_entry* report, int32_t max_report, int32_t* n_report, void* stream);
+/* Force a team size for every later solve of this handle (0 = the tuned table or
+ * the default; larger than the co-resident grid is clamped to it). */
+phipm_status phipm_set_team(phipm_handle* h, int32_t team);
+/* The team size a solve of this shape would use now (0 for invalid arguments). */
+int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n);
+/* Save / load the tuned table as JSON: {"sms": S, "entries": [{"precision": P,
+ * "kind": K, "log2n": L, "team": G, "ms": T}, ...]}.  Loading merges the entries
+ * into the handle's table when S equals this GPU's SM count and ignores the file
+ * otherwise; a file that cannot be read or parsed returns PHIPM_EINVAL and
+ * changes nothing. */
+phipm_status phipm_tune_save(phipm_handle* h, const char* path);
+phipm_status phipm_tune_load(phipm_handle* h, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "phipm.h"
@@ -143,6 +144,10 @@ struct phipm_handle {
   cudaEvent_t gev = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned char> gkey;
+  // team size per size class (precision, operator kind, floor(log2 n)), from the
+  // autotuner or a loaded cache; team_force overrides (0 = use the table / default)
+  std::map<int, std::pair<int, double>> tuned;
+  int team_force = 0;
 };
 
 static phipm_status fail(phipm_handle* h, phipm_status st, const std::string& msg) {
@@ -489,9 +494,26 @@ static bool any_csr(const DevProblem* probs, int count) {
 // ------------------------------------------------------------------------------------
 // single solve
 // ------------------------------------------------------------------------------------
-extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
-                                   const double* const* b, double tol, int32_t symm, double* u,
-                                   phipm_stats* stats, void* stream_) {
+static int size_class(int prec, int kind, int n) {
+  int lg = 0;
+  while (lg < 30 && (2ll << lg) <= (long long)n) ++lg;    // floor(log2 n)
+  return prec * 10000 + kind * 1000 + lg;
+}
+
+// CTAs that cooperate on one problem: forced, tuned for the size class, or the default
+// (every SM from n = 16384 on, else one CTA).
+static int choose_team(const phipm_handle* h, int prec, int kind, int n) {
+  const int gmax = h->grid_blocks[prec];
+  if (h->team_force > 0) return std::min(h->team_force, gmax);
+  const auto it = h->tuned.find(size_class(prec, kind, n));
+  if (it != h->tuned.end()) return std::min(it->second.first, gmax);
+  return n >= kGridMinN ? gmax : 1;
+}
+
+// team_req: 0 = choose_team, 1 = one CTA, G >= 2 = cooperative grid of G CTAs
+static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, const phipm_operator* A, int32_t p,
+                               const double* const* b, double tol, int32_t symm, double* u, phipm_stats* stats,
+                               void* stream_) {
   if (!h) return PHIPM_EINVAL;
   cudaStream_t stream = (cudaStream_t)stream_;
   long long nnz_model = 0;
@@ -528,8 +550,9 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
   DevResult* res_h = (DevResult*)h->res_host.p;
   DevResult* res_d = (DevResult*)h->res.p;
   const bool convert = prec != PHIPM_F64 && any_csr(&P, 1);
+  const int team = team_req > 0 ? std::min(team_req, h->grid_blocks[prec]) : choose_team(h, prec, A->kind, n);
 
-  if (n >= kGridMinN) {
+  if (team >= 2) {
     const long long ld = round_ld(n);
     const size_t vbytes = (size_t)M1 * ld * es, wbytes = (size_t)(p + 1) * ld * 8, ybytes = 2 * (size_t)ld * es;
     if (!h->ws.ensure(vbytes + wbytes + ybytes)) return fail(h, PHIPM_ENOMEM, "workspace");
@@ -537,7 +560,7 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
     P.W = (double*)((char*)h->ws.p + vbytes);
     P.Y = (char*)h->ws.p + vbytes + wbytes;
     P.ld = ld;
-    const int G = h->grid_blocks[prec];
+    const int G = team;
     if (!h->partials.ensure((size_t)2 * G * PM_PSTRIDE * sizeof(double))) return fail(h, PHIPM_ENOMEM, "partials");
     if (convert) {
       if (!h->probs.ensure(sizeof(DevProblem)) || !h->probs_host.ensure(sizeof(DevProblem)))
@@ -599,6 +622,12 @@ extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_o
   st = map_status(res_h->status);
   if (st != PHIPM_OK) return fail(h, st, status_text(st));
   return PHIPM_OK;
+}
+
+extern "C" phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
+                                   const double* const* b, double tol, int32_t symm, double* u,
+                                   phipm_stats* stats, void* stream) {
+  return solve_impl(h, 0, t_end, A, p, b, tol, symm, u, stats, stream);
 }
 
 // ------------------------------------------------------------------------------------
@@ -869,6 +898,127 @@ extern "C" phipm_status phipm_mlp_train(phipm_handle* h, float* w, float* m, flo
     e = cudaMemcpyAsync(losses, lossdev, (size_t)iters * sizeof(float), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   return e == cudaSuccess ? PHIPM_OK : cuda_fail(h, e, "mlp training");
+}
+
+// ------------------------------------------------------------------------------------
+// team-size autotuner: per size class, the number of CTAs that cooperate on a solve
+// ------------------------------------------------------------------------------------
+extern "C" phipm_status phipm_autotune(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
+                                      const double* const* b, double tol, int32_t symm, double* u,
+                                      phipm_tune_entry* report, int32_t max_report, int32_t* n_report,
+                                      void* stream) {
+  if (!h || !A) return PHIPM_EINVAL;
+  if (n_report) *n_report = 0;
+  const int prec = h->params.precision;
+  const int n = op_n(A);
+  if (n <= 0) return fail(h, PHIPM_EINVAL, "autotune needs n > 0");
+  const int gmax = h->grid_blocks[prec];
+  std::vector<int> cand = {1};
+  for (int g : {2, 4, 8, 16, 32})
+    if (g <= gmax && (long long)n >= 64ll * g) cand.push_back(g);
+  for (int div : {4, 2, 1}) {                 // fractions of the co-resident grid
+    const int g = gmax / div;
+    if (g >= 2 && (long long)n >= 64ll * g && std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+  }
+  int best = 0, k = 0;
+  double best_ms = 0.0;
+  for (int g : cand) {
+    phipm_stats st;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {       // the second run is timed (the first pays first-touch costs)
+      const phipm_status r = solve_impl(h, g, t_end, A, p, b, tol, symm, u, &st, stream);
+      if (r != PHIPM_OK) return r;
+      ms = (float)st.kernel_ms;
+    }
+    if (report && k < max_report) {
+      report[k].team = g;
+      report[k].kernel_ms = ms;
+    }
+    ++k;
+    if (best == 0 || ms < best_ms) { best = g; best_ms = ms; }
+  }
+  if (n_report) *n_report = std::min(k, max_report);
+  h->tuned[size_class(prec, A->kind, n)] = {best, best_ms};
+  return PHIPM_OK;
+}
+
+extern "C" phipm_status phipm_set_team(phipm_handle* h, int32_t team) {
+  if (!h) return PHIPM_EINVAL;
+  if (team < 0) return fail(h, PHIPM_EINVAL, "team < 0");
+  h->team_force = team;
+  return PHIPM_OK;
+}
+
+extern "C" int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n) {
+  if (!h || precision < 0 || precision > 2 || (kind != 0 && kind != 1) || n <= 0) return 0;
+  return choose_team(h, precision, kind, n);
+}
+
+// Cache file: one JSON object, {"sms": S, "entries": [{"precision": P, "kind": K,
+// "log2n": L, "team": G, "ms": T}, ...]}.  Entries for another SM count are ignored
+// on load.
+extern "C" phipm_status phipm_tune_save(phipm_handle* h, const char* path) {
+  if (!h || !path) return PHIPM_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(h, PHIPM_EINVAL, std::string("cannot write ") + path);
+  fprintf(f, "{\"sms\": %d, \"entries\": [", h->num_sms);
+  bool first = true;
+  for (const auto& kv : h->tuned) {
+    const int key = kv.first;
+    fprintf(f, "%s\n  {\"precision\": %d, \"kind\": %d, \"log2n\": %d, \"team\": %d, \"ms\": %.6g}", first ? "" : ",",
+            key / 10000, (key / 1000) % 10, key % 1000, kv.second.first, kv.second.second);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  const bool ok = fclose(f) == 0;
+  return ok ? PHIPM_OK : fail(h, PHIPM_EINVAL, std::string("cannot write ") + path);
+}
+
+static bool json_int(const std::string& obj, const char* key, long long& out) {
+  const std::string k = std::string("\"") + key + "\"";
+  size_t i = obj.find(k);
+  if (i == std::string::npos) return false;
+  i = obj.find(':', i + k.size());
+  if (i == std::string::npos) return false;
+  ++i;
+  while (i < obj.size() && (obj[i] == ' ' || obj[i] == '\t' || obj[i] == '\n' || obj[i] == '\r')) ++i;
+  char* end = nullptr;
+  const long long v = strtoll(obj.c_str() + i, &end, 10);
+  if (end == obj.c_str() + i) return false;
+  out = v;
+  return true;
+}
+
+extern "C" phipm_status phipm_tune_load(phipm_handle* h, const char* path) {
+  if (!h || !path) return PHIPM_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(h, PHIPM_EINVAL, std::string("cannot read ") + path);
+  std::string text;
+  char buf[4096];
+  size_t r;
+  while ((r = fread(buf, 1, sizeof(buf), f)) > 0 && text.size() < (1u << 20)) text.append(buf, r);
+  fclose(f);
+  long long sms = 0;
+  const size_t lb = text.find('[');
+  if (lb == std::string::npos || !json_int(text.substr(0, lb), "sms", sms))
+    return fail(h, PHIPM_EINVAL, "tuning cache: no sms / entries");
+  if (sms != h->num_sms) return PHIPM_OK;     // tuned on another GPU: nothing applies
+  std::map<int, std::pair<int, double>> add;
+  size_t pos = lb;
+  while (true) {
+    const size_t a = text.find('{', pos), z = (a == std::string::npos) ? a : text.find('}', a);
+    if (a == std::string::npos || z == std::string::npos) break;
+    const std::string obj = text.substr(a, z - a + 1);
+    long long pr, kd, lg, tm;
+    if (!json_int(obj, "precision", pr) || !json_int(obj, "kind", kd) || !json_int(obj, "log2n", lg) ||
+        !json_int(obj, "team", tm) || pr < 0 || pr > 2 || kd < 0 || kd > 1 || lg < 0 || lg > 30 || tm < 1 ||
+        tm > 1 << 20)
+      return fail(h, PHIPM_EINVAL, "tuning cache: malformed entry");
+    add[(int)(pr * 10000 + kd * 1000 + lg)] = {(int)tm, 0.0};
+    pos = z + 1;
+  }
+  for (const auto& kv : add) h->tuned[kv.first] = kv.second;
+  return PHIPM_OK;
 }
 
 // ------------------------------------------------------------------------------------

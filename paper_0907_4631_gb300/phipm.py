@@ -54,6 +54,10 @@ class TraceRecordC(ctypes.Structure):
                 ("rejects_prev", c_int32)]
 
 
+class TuneEntryC(ctypes.Structure):
+    _fields_ = [("team", c_int32), ("reserved", c_int32), ("kernel_ms", c_double)]
+
+
 class ParamsC(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("delta", c_double), ("m_init", c_int32), ("m_max", c_int32),
                 ("theta13", c_double), ("breakdown_tol", c_double), ("max_steps", c_int64),
@@ -114,6 +118,18 @@ def lib(build_if_needed: bool = True):
     L.phipm_mlp_train.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32,
                                   c_int64, ctypes.c_float, ctypes.POINTER(ctypes.c_float), c_void_p]
     L.phipm_mlp_train.restype = c_int32
+    L.phipm_autotune.argtypes = [c_void_p, c_double, ctypes.POINTER(OperatorC), c_int32, ctypes.POINTER(c_void_p),
+                                 c_double, c_int32, c_void_p, ctypes.POINTER(TuneEntryC), c_int32,
+                                 ctypes.POINTER(c_int32), c_void_p]
+    L.phipm_autotune.restype = c_int32
+    L.phipm_set_team.argtypes = [c_void_p, c_int32]
+    L.phipm_set_team.restype = c_int32
+    L.phipm_team_for.argtypes = [c_void_p, c_int32, c_int32, c_int32]
+    L.phipm_team_for.restype = c_int32
+    L.phipm_tune_save.argtypes = [c_void_p, ctypes.c_char_p]
+    L.phipm_tune_save.restype = c_int32
+    L.phipm_tune_load.argtypes = [c_void_p, ctypes.c_char_p]
+    L.phipm_tune_load.restype = c_int32
     _LIB = L
     return L
 
@@ -250,6 +266,34 @@ class Phipm:
         if check:
             self._check(st)
         return u, stats.as_dict(), st
+
+    def autotune(self, t_end: float, A: DeviceOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,
+                 stream=None) -> list:
+        """phipm_autotune: time each candidate team size on this problem and keep the fastest
+        for its size class.  Returns [(team, kernel_ms), ...] in the order tried."""
+        import torch
+        n = A.n
+        p = len(b) - 1
+        u = out if out is not None else torch.empty(n, dtype=torch.float64, device=b[0].device)
+        bp = (c_void_p * (p + 1))(*[x.data_ptr() for x in b])
+        rep = (TuneEntryC * 16)()
+        cnt = c_int32(0)
+        st = lib().phipm_autotune(self.h, float(t_end), ctypes.byref(A.c), p, bp, float(tol), int(symm),
+                                  c_void_p(u.data_ptr()), rep, 16, ctypes.byref(cnt), _stream_ptr(stream))
+        self._check(st)
+        return [(rep[i].team, rep[i].kernel_ms) for i in range(cnt.value)]
+
+    def set_team(self, team: int):
+        self._check(lib().phipm_set_team(self.h, int(team)))
+
+    def team_for(self, kind: int, n: int) -> int:
+        return lib().phipm_team_for(self.h, self.params.precision, int(kind), int(n))
+
+    def tune_save(self, path: str):
+        self._check(lib().phipm_tune_save(self.h, str(path).encode()))
+
+    def tune_load(self, path: str):
+        self._check(lib().phipm_tune_load(self.h, str(path).encode()))
 
     def solve_host(self, t_end: float, A: HostOperator, b: list, tol: float = 1e-7, symm: int = -1, out=None,
                    stream=None, check: bool = True):

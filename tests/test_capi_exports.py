@@ -35,7 +35,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     import os
     import subprocess
     structs = {"phipm_csr": pm.CsrC, "phipm_stencil": pm.StencilC, "phipm_operator": pm.OperatorC,
-               "phipm_stats": pm.StatsC, "phipm_params": pm.ParamsC, "phipm_trace_record": pm.TraceRecordC}
+               "phipm_stats": pm.StatsC, "phipm_params": pm.ParamsC, "phipm_trace_record": pm.TraceRecordC,
+               "phipm_tune_entry": pm.TuneEntryC}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "phipm.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
@@ -69,3 +70,13 @@ def test_invalid_params_rejected_without_gpu():
     h = ctypes.c_void_p()
     assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
     assert not h.value
+
+
+def test_tuning_entry_points_reject_null_handles(tmp_path):
+    """Host-side argument checks of the autotuner's cache calls (no GPU needed)."""
+    L = pm.lib()
+    path = str(tmp_path / "tune.json").encode()
+    assert L.phipm_tune_save(None, path) == pm.EINVAL
+    assert L.phipm_tune_load(None, path) == pm.EINVAL
+    assert L.phipm_set_team(None, 4) == pm.EINVAL
+    assert L.phipm_team_for(None, pm.F64, 0, 1000) == 0
