@@ -94,12 +94,15 @@ def measured_peaks():
 
 
 def algorithmic_bytes(pr, stats, precision) -> float:
-    """SpMV + Arnoldi bytes of one solve (per-step model; see DESIGN.md).
+    """SpMV + Arnoldi bytes of one solve (per-step model).
 
-    CGS2 step j touches j+1 basis vectors four times (two dot passes, two
-    update passes): 4 (j+1) s n bytes, summed as 4 s n gs_vectors.  Each Krylov
-    step also runs one SpMV (CSR: 12 nnz + 4 (n+1) + 2 s n for the x read and
-    the y write; stencil: 2 s n) and writes the new basis vector (s n)."""
+    An Arnoldi step j (lagged Gram-Schmidt) reads the j basis vectors twice (the
+    dot pass and the fused update), summed as 2 s n gs_vectors; it reads the
+    candidate and A times the candidate twice and writes the new basis vector
+    and the next candidate (6 s n), and runs one SpMV (CSR: 12 nnz + 4 (n+1) +
+    2 s n for the x read and the y write; stencil: 2 s n).  A Lanczos step reads
+    v_j for the dot, v_{j-1}, v_j and y for the update and writes y, reads y for
+    the norm, and writes the next basis vector."""
     n = pr.n
     s = 4 if precision == "f32" else 8
     if hasattr(pr.op, "rowptr"):
@@ -108,10 +111,10 @@ def algorithmic_bytes(pr, stats, precision) -> float:
         spmv = 2 * s * n
     kry = stats["krylov_steps"]
     gs = stats["gs_vectors"]
-    if gs == 0:   # Lanczos: t_jj dot (v_j, y), three-term update (v_{j-1}, v_j, y r/w), norm
+    if gs == 0:   # Lanczos
         per_step = spmv + s * n * (2 + 4) + s * n
         return kry * per_step
-    return 4.0 * s * n * gs + kry * (spmv + s * n)
+    return 2.0 * s * n * gs + kry * (spmv + 6.0 * s * n)
 
 
 class ClockSampler:

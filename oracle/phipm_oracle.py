@@ -18,7 +18,7 @@ It follows the paper step by step, slow and plain:
     Eqs. (4), (5), (8), and Algorithms 3 and 4.
 
 Readings where the paper is silent, garbled or contradicts itself
-(each also listed in the design doc):
+(the same readings hold for the CUDA path):
   R2  augmented matrix has size m+p+1; phi_j(tau H) e_1 is column m+j-1
       (0-based); tau multiplies only the H block.
   R3  Lanczos: t_{j+1,j} = t_{j,j+1} = ||w||, v_{j+1} = w / t_{j+1,j}.

@@ -18,6 +18,7 @@
 struct PmScal {
   double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
   double fnorm, last_tau, omega, last_omega, m_new;
+  double fz, fw, fab, dcoef;            // lagged Gram-Schmidt: z.z, z.w, a.b, d
   double tl[PM_MAXP + 1];
   df32 inv2;
   float invf;
@@ -31,11 +32,15 @@ struct PmScal {
 struct PmShared {
   double H[(PM_MAXM + 1) * PM_MAXM];   // H[i * PM_MAXM + j], Hessenberg / tridiagonal
   double red[PM_WARPS][8];
-  double coef[PM_NSLOT + 2];           // reduced sums of the current phase
-  double h1[PM_NSLOT];                 // first-pass Gram-Schmidt coefficients (H = h1 + h2)
+  double coef[2 * PM_NSLOT + 4];       // reduced sums of the current phase
+  double h1[PM_NSLOT];                 // Gram-Schmidt coefficients a (candidate's second pass)
+  double hb[PM_NSLOT];                 // Gram-Schmidt coefficients b (new vector's first pass)
   double hdd[PM_NSLOT];                // coefficients of the current update (FP64 basis)
   float hf[PM_NSLOT];                  // ... as float (FP32 basis)
   df32 hd[PM_NSLOT];                   // ... as float pairs (float-pair basis)
+  double hdd2[PM_NSLOT];               // second coefficient set of a fused two-output update
+  float hf2[PM_NSLOT];
+  df32 hd2[PM_NSLOT];
   double phi0[PM_NA], phi1[PM_NA];     // phi_p(tau H) e1 and phi_{p+1}(tau H) e1
   double ucoef[PM_NSLOT + PM_MAXP + 1];
   float ucf[PM_NSLOT];
@@ -54,7 +59,7 @@ struct PmWork {
   double* expm;         // team-shared exponential scratch: PM_EXPM_DOUBLES doubles
 };
 
-#define PM_PSTRIDE (PM_NSLOT + 2)
+#define PM_PSTRIDE (2 * PM_NSLOT + 4)
 
 // ------------------------------------------------------------------------------------
 // team reductions of K values held in s.coef[0..K) by each CTA
@@ -510,6 +515,237 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
   }
 }
 
+// Two dot products per left vector in one pass, for the lagged Gram-Schmidt step:
+// with L_i = V_i (i < nv) and L_nv = z, s.coef[i] = L_i . z and
+// s.coef[nv + 1 + i] = L_i . w (i <= nv).  Runs per warp as in dots_cta; each
+// segment leaves two warp-reduced partials in s.dred (even / odd slots).
+template <class S>
+__device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* __restrict__ z,
+                                             const S* __restrict__ w, int a, int b, double& dz, double& dw) {
+  typedef Elem<S> E;
+  typedef typename E::Acc Acc;
+  const int lane = threadIdx.x & 31;
+  Acc z0 = E::zero(), z1 = E::zero(), w0 = E::zero(), w1 = E::zero();
+  const int qa = min(b, (a + 3) & ~3);
+  const int qb = max(qa, b & ~3);
+  if (a + lane < qa) { E::dot(z1, v[a + lane], z[a + lane]); E::dot(w1, v[a + lane], w[a + lane]); }
+  int e = qa + 4 * lane;
+  for (; e + 128 + 3 < qb; e += 256) {        // two quads of each operand per lane in flight
+    Quad<S> v0, v1, z0q, z1q, w0q, w1q;
+    v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
+    v1.load(v + e + 128); z1q.load(z + e + 128); w1q.load(w + e + 128);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      E::dot(z0, v0.x[k], z0q.x[k]);
+      E::dot(w0, v0.x[k], w0q.x[k]);
+      E::dot(z1, v1.x[k], z1q.x[k]);
+      E::dot(w1, v1.x[k], w1q.x[k]);
+    }
+  }
+  for (; e + 3 < qb; e += 128) {
+    Quad<S> v0, z0q, w0q;
+    v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { E::dot(z0, v0.x[k], z0q.x[k]); E::dot(w0, v0.x[k], w0q.x[k]); }
+  }
+  if (qb + lane < b) { E::dot(z0, v[qb + lane], z[qb + lane]); E::dot(w0, v[qb + lane], w[qb + lane]); }
+  dz = E::val(z0) + E::val(z1);
+  dw = E::val(w0) + E::val(w1);
+}
+
+template <class S>
+__device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                          const S* __restrict__ w, int lo, int hi, PmShared& s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long rows = hi - lo;
+  const int nvec = nv + 1;
+  const long long total = (long long)nvec * rows;
+  if (total == 0) {
+    for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
+    __syncthreads();
+    return;
+  }
+  // as in dots_cta: a run meets fewer than 12 vectors, so 2 x 12 slots fit PM_DSEG
+  const long long run = (((total + PM_WARPS - 1) / PM_WARPS) + 3) & ~3ll;
+  long long f = (long long)warp * run;
+  const long long fend = min(total, f + run);
+  if (f < fend) {
+    int i = (int)(f / rows);
+    long long r0 = f - (long long)i * rows;
+    for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
+      const long long r1 = min(rows, r0 + (fend - f));
+      const S* v = (i < nv) ? V + (size_t)i * ld : z;
+      double dz, dw;
+      dot_segment2<S>(v, z, w, lo + (int)r0, lo + (int)r1, dz, dw);
+      dz = pm_warp_sum(dz);
+      dw = pm_warp_sum(dw);
+      if (lane == 0) {
+        s.dred[warp * PM_DSEG + 2 * seg] = dz;
+        s.dred[warp * PM_DSEG + 2 * seg + 1] = dw;
+      }
+      f += r1 - r0;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    const long long fa = (long long)i * rows, fb = fa + rows - 1;
+    double tz = 0.0, tw = 0.0;
+    for (long long w2 = fa / run; w2 <= fb / run && w2 < PM_WARPS; ++w2) {
+      const int sl = (int)w2 * PM_DSEG + 2 * (int)(i - (w2 * run) / rows);
+      tz += s.dred[sl];
+      tw += s.dred[sl + 1];
+    }
+    s.coef[i] = tz;
+    s.coef[nvec + i] = tw;
+  }
+  __syncthreads();
+}
+
+// Fused update of the lagged Gram-Schmidt step over this CTA's rows:
+//   q = (z - sum_{i<nv} a_i V_i) * inv                  (written to qout when qout != 0)
+//   z' = (w - sum_{i<nv} b_i V_i - d q) * inv            (written to zout when zout != 0)
+// with q = z when reorth is false (z is then the normalised basis vector itself).
+// Four consecutive rows per thread, four basis quads in flight, each loaded once for
+// both sums.  zout may alias z (each thread reads its rows of z before writing them).
+template <class S>
+__device__ __forceinline__ void upd2_finish(Quad<S>& q, Quad<S>& zn, const Quad<S>& zq, const Quad<S>& wq,
+                                            typename Elem<S>::Coef d, typename Elem<S>::Coef inv, bool reorth) {
+  typedef Elem<S> E;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if constexpr (E::kind == 2) {
+      q.x[k] = reorth ? df_mul(q.x[k], inv) : zq.x[k];
+      zn.x[k] = df_mul(df_sub(zn.x[k], df_mul(d, q.x[k])), inv);
+    } else {
+      q.x[k] = reorth ? q.x[k] * (S)inv : zq.x[k];
+      zn.x[k] = fma(-(S)d, q.x[k], zn.x[k]) * (S)inv;
+    }
+  }
+}
+
+template <class S>
+__device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, const typename Elem<S>::Coef* ca,
+                             const typename Elem<S>::Coef* cb, typename Elem<S>::Coef d, typename Elem<S>::Coef inv,
+                             const S* z, const S* __restrict__ w, S* qout, S* zout, bool reorth, int lo, int hi) {
+  typedef Elem<S> E;
+  for (int r = lo + 4 * threadIdx.x; r < hi; r += 4 * blockDim.x) {
+    if (r + 3 < hi) {
+      Quad<S> q, zn, zq, wq;
+      if constexpr (E::kind == 2) {
+        F2Acc sa[4], sb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { sa[k] = f2_zero(); sb[k] = f2_zero(); }
+        int i = 0;
+        for (; i + 3 < nv; i += 4) {
+          Quad<S> v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u].load(V + (size_t)(i + u) * ld + r);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const df32 au = ca[i + u], bu = cb[i + u];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (reorth) f2_add_prod(sa[k], au, v[u].x[k]);
+              f2_add_prod(sb[k], bu, v[u].x[k]);
+            }
+          }
+        }
+        for (; i < nv; ++i) {
+          Quad<S> v0;
+          v0.load(V + (size_t)i * ld + r);
+          const df32 au = ca[i], bu = cb[i];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (reorth) f2_add_prod(sa[k], au, v0.x[k]);
+            f2_add_prod(sb[k], bu, v0.x[k]);
+          }
+        }
+        zq.load(z + r);
+        wq.load(w + r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          q.x[k] = df_sub(zq.x[k], f2_round(sa[k]));
+          zn.x[k] = df_sub(wq.x[k], f2_round(sb[k]));
+        }
+      } else {
+        zq.load(z + r);
+        wq.load(w + r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { q.x[k] = zq.x[k]; zn.x[k] = wq.x[k]; }
+        int i = 0;
+        for (; i + 3 < nv; i += 4) {
+          Quad<S> v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u].load(V + (size_t)(i + u) * ld + r);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const S au = (S)ca[i + u], bu = (S)cb[i + u];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (reorth) q.x[k] = fma(-au, v[u].x[k], q.x[k]);
+              zn.x[k] = fma(-bu, v[u].x[k], zn.x[k]);
+            }
+          }
+        }
+        for (; i < nv; ++i) {
+          Quad<S> v0;
+          v0.load(V + (size_t)i * ld + r);
+          const S au = (S)ca[i], bu = (S)cb[i];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (reorth) q.x[k] = fma(-au, v0.x[k], q.x[k]);
+            zn.x[k] = fma(-bu, v0.x[k], zn.x[k]);
+          }
+        }
+      }
+      upd2_finish<S>(q, zn, zq, wq, d, inv, reorth);
+      if (qout) q.store(qout + r);
+      if (zout) zn.store(zout + r);
+    } else {
+      for (int t = r; t < hi; ++t) {       // ragged end: one row at a time
+        Quad<S> q, zn, zq, wq;
+        if constexpr (E::kind == 2) {
+          F2Acc sa = f2_zero(), sb = f2_zero();
+          for (int i = 0; i < nv; ++i) {
+            const df32 vi = V[(size_t)i * ld + t];
+            if (reorth) f2_add_prod(sa, ca[i], vi);
+            f2_add_prod(sb, cb[i], vi);
+          }
+          zq.x[0] = z[t];
+          wq.x[0] = w[t];
+          q.x[0] = df_sub(zq.x[0], f2_round(sa));
+          zn.x[0] = df_sub(wq.x[0], f2_round(sb));
+        } else {
+          zq.x[0] = z[t];
+          wq.x[0] = w[t];
+          S qa = zq.x[0], zb = wq.x[0];
+          for (int i = 0; i < nv; ++i) {
+            const S vi = V[(size_t)i * ld + t];
+            if (reorth) qa = fma(-(S)ca[i], vi, qa);
+            zb = fma(-(S)cb[i], vi, zb);
+          }
+          q.x[0] = qa;
+          zn.x[0] = zb;
+        }
+#pragma unroll
+        for (int k = 1; k < 4; ++k) { q.x[k] = q.x[0]; zn.x[k] = zn.x[0]; zq.x[k] = zq.x[0]; wq.x[k] = wq.x[0]; }
+        upd2_finish<S>(q, zn, zq, wq, d, inv, reorth);
+        if (qout) qout[t] = q.x[0];
+        if (zout) zout[t] = zn.x[0];
+      }
+    }
+  }
+}
+
+// Out-of-line copy for the rarely taken paths (second projection, completing the
+// last candidate), so that they do not add to the register pressure of the main loop.
+template <class S>
+__device__ __noinline__ void update_rows2_cold(const S* V, long long ld, int nv, const typename Elem<S>::Coef* ca,
+                                               typename Elem<S>::Coef inv, const S* z, const S* w, S* qout,
+                                               int lo, int hi) {
+  update_rows2<S>(V, ld, nv, ca, ca, Elem<S>::coef(0.0), inv, z, w, qout, nullptr, true, lo, hi);
+}
+
 // ------------------------------------------------------------------------------------
 // the exponential of the augmented matrix, spread over the team's CTAs
 // ------------------------------------------------------------------------------------
@@ -769,6 +1005,10 @@ template <class S> __device__ __forceinline__ typename Elem<S>::Coef* coef_array
 template <> __device__ __forceinline__ double* coef_array<double>(PmShared& s) { return s.hdd; }
 template <> __device__ __forceinline__ float* coef_array<float>(PmShared& s) { return s.hf; }
 template <> __device__ __forceinline__ df32* coef_array<df32>(PmShared& s) { return s.hd; }
+template <class S> __device__ __forceinline__ typename Elem<S>::Coef* coef_array2(PmShared& s);
+template <> __device__ __forceinline__ double* coef_array2<double>(PmShared& s) { return s.hdd2; }
+template <> __device__ __forceinline__ float* coef_array2<float>(PmShared& s) { return s.hf2; }
+template <> __device__ __forceinline__ df32* coef_array2<df32>(PmShared& s) { return s.hd2; }
 template <class S> __device__ __forceinline__ typename Elem<S>::Coef scal_inv(const PmScal& c);
 template <> __device__ __forceinline__ double scal_inv<double>(const PmScal& c) { return c.inv; }
 template <> __device__ __forceinline__ float scal_inv<float>(const PmScal& c) { return c.invf; }
@@ -1004,7 +1244,209 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         // ---------------- Krylov extension (a3/a4) to m steps
         const int target = c.invariant ? c.kcur : c.m;
         const int j0 = c.kcur;   // first step of this extension
-        if (j0 < target) {
+        if (j0 < target && !c.lanczos) {
+          // Arnoldi with lagged (delayed) classical Gram-Schmidt and reorthogonalisation:
+          // iteration j applies A to the candidate z for v_j (projected once, not yet
+          // reorthogonalised or normalised), and one pass over V_0..V_{j-1} gives both
+          // the candidate's second-pass coefficients a = V^T z (with z.z) and the new
+          // vector's coefficients b = V^T w (with z.w), w = A z.  With nu = ||z - V a||
+          // (Pythagoras), v_j = (z - V a) / nu, column j-1 of H gains a and nu, and by
+          // the Arnoldi relation A v_j = (w - V_{j+1} H a) / nu, whose projections are
+          // known without touching the vectors again:
+          //   H[i][j] (first pass) = (b_i - (H a)_i) / nu,   i < j,
+          //   H[j][j] (first pass) = (d - (H a)_j) / nu,     d = (z.w - a.b) / nu,
+          //   next candidate       = (w - V b - d v_j) / nu.
+          // One pass of dot products, one team reduction, one fused update and one team
+          // barrier per step, against two of each for classical Gram-Schmidt applied
+          // twice.  The last candidate is completed after the loop.  At the first
+          // iteration of an extension the candidate is v_j itself (a = 0, nu = 1).
+          S* Z = Y;                          // candidate (own rows + halo)
+          S* Wv = Y + ld;                    // A applied to the candidate
+          C* ca = coef_array<S>(s);
+          C* cb = coef_array2<S>(s);
+          for (int j = j0; j < target; ++j) {
+            const bool zfinal = (j == j0);
+            const S* zp = zfinal ? V + (size_t)j * ld : Z;
+            if (j == 0) {
+              const C sc = scal_inv<S>(c);   // 1/beta
+              DLoadAs<S, Team::multi> xl{wp, lo, hi};
+              for (int r = lo + tid; r < hi; r += nth) {
+                V[r] = E::from_d(wp[r] * c.inv);
+                Wv[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
+              }
+            } else {
+              VecLoad<S, Team::multi> xl{zp, lo, hi};
+              for (int r = lo + tid; r < hi; r += nth) Wv[r] = spmv_row<S>(P.A, r, xl);
+            }
+            matvecs += 1;
+            kry_steps += 1;
+            gs_vectors += j;
+            __syncthreads();
+            dots2_cta<S>(V, ld, j, zp, Wv, lo, hi, s);
+            PM_SUM_OR_FAIL(2 * (j + 1));
+            // scalars by one warp (||a||^2, a.b); a and b copied by every thread
+            if (tid < 32) {
+              double aa = 0.0, ab = 0.0;
+              if (!zfinal)
+                for (int k = tid; k < j; k += 32) {
+                  const double ak = s.coef[k];
+                  aa = fma(ak, ak, aa);
+                  ab = fma(ak, s.coef[j + 1 + k], ab);
+                }
+              aa = pm_warp_sum(aa);
+              ab = pm_warp_sum(ab);
+              if (tid == 0) {
+                c.fz = s.coef[j];                // z.z
+                c.fw = s.coef[2 * j + 1];        // z.w
+                c.fab = ab;                      // a.b
+                c.hn = zfinal ? 1.0 : c.fz - aa; // nu^2 by Pythagoras
+                c.measure = (zfinal || aa <= 0.25 * c.fz) ? 0 : 1;   // else: project the candidate again
+              }
+            }
+            for (int k = tid; k < j; k += nth) {
+              const double ak = zfinal ? 0.0 : s.coef[k], bk = s.coef[j + 1 + k];
+              s.h1[k] = ak;
+              s.hb[k] = bk;
+              ca[k] = E::coef(ak);
+              cb[k] = E::coef(bk);
+            }
+            __syncthreads();
+            if (c.measure) {
+              // q0 = z - V a into v_j's slot, then its own projections a2 and norm
+              update_rows2_cold<S>(V, ld, j, ca, E::coef(1.0), zp, Wv, V + (size_t)j * ld, lo, hi);
+              __syncthreads();
+              dots_cta<S>(V, ld, j, V + (size_t)j * ld, lo, hi, true, s);
+              PM_SUM_OR_FAIL(j + 1);
+              if (tid < 32) {
+                double aa = 0.0;
+                for (int k = tid; k < j; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
+                aa = pm_warp_sum(aa);
+                if (tid == 0) {
+                  const double q0 = s.coef[j];
+                  c.hn = (aa <= 0.25 * q0) ? q0 - aa : 0.0;   // still not orthogonal: numerically in the span
+                }
+              }
+              for (int k = tid; k < j; k += nth) {
+                s.h1[k] += s.coef[k];
+                ca[k] = E::coef(s.h1[k]);
+              }
+              __syncthreads();
+              if (tid < 32) {
+                double ab = 0.0;
+                for (int k = tid; k < j; k += 32) ab = fma(s.h1[k], s.hb[k], ab);
+                ab = pm_warp_sum(ab);
+                if (tid == 0) c.fab = ab;
+              }
+              __syncthreads();
+            }
+            if (tid == 0) {
+              c.hn = sqrt(fmax(c.hn, 0.0));
+              if (!zfinal && c.hn <= c.bd_abs) {   // happy breakdown (R12): span(v_0..v_{j-1}) is invariant
+                c.invariant = 1;
+                c.kcur = j;
+                c.hn = 0.0;
+              } else {
+                set_inv(c, c.hn);
+                c.dcoef = (c.fw - c.fab) * c.inv;  // d = (z.w - a.b) / nu
+              }
+            }
+            __syncthreads();
+            if (c.invariant) {
+              for (int k = tid; k < j; k += nth) s.H[k * PM_MAXM + j - 1] += s.h1[k];
+              if (tid == 0) s.H[j * PM_MAXM + j - 1] = 0.0;
+              __syncthreads();
+              break;
+            }
+            // columns j-1 (second pass, subdiagonal nu) and j (first pass) of H, row l by
+            // thread l; H is next read after later barriers, so the update starts at once
+            {
+              // one warp per row l, lanes splitting the sum (short FP64 dependency chains)
+              const int warp = tid >> 5, lane = tid & 31;
+              for (int l = warp; l <= j; l += PM_WARPS) {
+                if (l < j) {
+                  double g = 0.0;                // (H a)_l over the Hessenberg columns l-1 .. j-2
+                  for (int i = max(l - 1, 0) + lane; i < j - 1; i += 32) g = fma(s.H[l * PM_MAXM + i], s.h1[i], g);
+                  g = pm_warp_sum(g);
+                  if (lane == 0) {
+                    double hl = s.H[l * PM_MAXM + j - 1];
+                    if (!zfinal) {
+                      hl += s.h1[l];
+                      s.H[l * PM_MAXM + j - 1] = hl;
+                    }
+                    g = fma(hl, s.h1[j - 1], g);
+                    s.H[l * PM_MAXM + j] = (s.hb[l] - g) * c.inv;
+                  }
+                } else if (lane == 0) {
+                  if (j > 0 && !zfinal) s.H[j * PM_MAXM + j - 1] = c.hn;
+                  const double g = (j > 0) ? c.hn * s.h1[j - 1] : 0.0;
+                  s.H[j * PM_MAXM + j] = (c.dcoef - g) * c.inv;
+                }
+              }
+            }
+            update_rows2<S>(V, ld, j, ca, cb, E::coef(c.dcoef), scal_inv<S>(c), zp, Wv,
+                            zfinal ? nullptr : V + (size_t)j * ld, Z, !zfinal, lo, hi);
+            PM_SYNC_OR_FAIL();                 // the next SpMV reads other CTAs' rows of the candidate
+            if (tid == 0) c.kcur = j;          // complete columns 0 .. j-1
+          }
+          if (!c.invariant) {
+            // complete the last candidate: v_target and column target-1
+            const int nq = target;
+            gs_vectors += nq;
+            dots_cta<S>(V, ld, nq, Z, lo, hi, true, s);
+            PM_SUM_OR_FAIL(nq + 1);
+            for (int k = tid; k < nq; k += nth) s.h1[k] = s.coef[k];
+            if (tid < 32) {
+              double aa = 0.0;
+              for (int k = tid; k < nq; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
+              aa = pm_warp_sum(aa);
+              if (tid == 0) {
+                c.fz = s.coef[nq];
+                c.hn = c.fz - aa;
+                c.measure = (aa <= 0.25 * c.fz) ? 0 : 1;
+              }
+            }
+            __syncthreads();
+            if (c.measure) {
+              for (int k = tid; k < nq; k += nth) ca[k] = E::coef(s.h1[k]);
+              __syncthreads();
+              update_rows2_cold<S>(V, ld, nq, ca, E::coef(1.0), Z, Wv, V + (size_t)nq * ld, lo, hi);
+              __syncthreads();
+              dots_cta<S>(V, ld, nq, V + (size_t)nq * ld, lo, hi, true, s);
+              PM_SUM_OR_FAIL(nq + 1);
+              if (tid < 32) {
+                double aa = 0.0;
+                for (int k = tid; k < nq; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
+                aa = pm_warp_sum(aa);
+                if (tid == 0) {
+                  const double q0 = s.coef[nq];
+                  c.hn = (aa <= 0.25 * q0) ? q0 - aa : 0.0;
+                }
+              }
+              for (int k = tid; k < nq; k += nth) s.h1[k] += s.coef[k];
+              __syncthreads();
+            }
+            for (int k = tid; k < nq; k += nth) s.H[k * PM_MAXM + nq - 1] += s.h1[k];
+            if (tid == 0) {
+              c.hn = sqrt(fmax(c.hn, 0.0));
+              c.kcur = nq;
+              if (c.hn <= c.bd_abs) {          // happy breakdown (R12)
+                s.H[nq * PM_MAXM + nq - 1] = 0.0;
+                c.hn = 0.0;
+                c.invariant = 1;
+              } else {
+                s.H[nq * PM_MAXM + nq - 1] = c.hn;
+                set_inv(c, c.hn);
+              }
+            }
+            __syncthreads();
+            if (!c.invariant) {
+              for (int k = tid; k < nq; k += nth) ca[k] = E::coef(s.h1[k]);
+              __syncthreads();
+              update_rows2_cold<S>(V, ld, nq, ca, scal_inv<S>(c), Z, Wv, V + (size_t)nq * ld, lo, hi);
+              __syncthreads();
+            }
+          }
+        } else if (j0 < target) {
           for (int j = j0; j < target; ++j) {
             // phase A: write v_j (my rows), y = A v_j
             S* ycur = Y + (size_t)(j & 1) * ld;
@@ -1029,7 +1471,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             matvecs += 1;
             kry_steps += 1;
             __syncthreads();
-            if (c.lanczos) {
+            {
               // Algorithm 2: t_jj = v_j^T y ; y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
               dots_cta<S>(V + (size_t)j * ld, ld, 1, ycur, lo, hi, false, s);
               PM_SUM_OR_FAIL(1);
@@ -1050,50 +1492,6 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
                 s.H[(j + 1) * PM_MAXM + j] = hn;
                 if (j + 1 < PM_MAXM) s.H[j * PM_MAXM + j + 1] = hn;
                 c.hn = hn;
-              }
-            } else {
-              // CGS2: h1 = V^T y ; y -= V h1 ; (h2, ||y||^2) ; y -= V h2 ; h = h1 + h2 ;
-              // ||y_final||^2 = ||y||^2 - ||h2||^2 (V orthonormal) replaces the last
-              // reduction by a plain team barrier
-              const int nv = j + 1;
-              gs_vectors += nv;
-              dots_cta<S>(V, ld, nv, ycur, lo, hi, false, s);
-              PM_SUM_OR_FAIL(nv);
-              for (int k = tid; k < nv; k += nth) { s.h1[k] = s.coef[k]; hc[k] = E::coef(s.coef[k]); }
-              __syncthreads();
-              update_rows<S>(ycur, V, ld, nv, hc, lo, hi);
-              __syncthreads();
-              dots_cta<S>(V, ld, nv, ycur, lo, hi, true, s);
-              PM_SUM_OR_FAIL(nv + 1);
-              for (int k = tid; k < nv; k += nth) {
-                const double h2 = s.coef[k];
-                s.H[k * PM_MAXM + j] = s.h1[k] + h2;
-                hc[k] = E::coef(h2);
-              }
-              if (tid < 32) {   // ||h2||^2 by one warp
-                double a = 0.0;
-                for (int k = tid; k < nv; k += 32) a = fma(s.coef[k], s.coef[k], a);
-                a = pm_warp_sum(a);
-                if (tid == 0) {
-                  const double y0n = s.coef[nv];
-                  c.hn = y0n - a;                           // squared norm by Pythagoras
-                  c.measure = (a <= 0.25 * y0n) ? 0 : 1;    // not orthogonal enough: measure it
-                }
-              }
-              __syncthreads();
-              update_rows<S>(ycur, V, ld, nv, hc, lo, hi);
-              __syncthreads();
-              if (c.measure) {
-                dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
-                PM_SUM_OR_FAIL(1);
-                if (tid == 0) c.hn = s.coef[0];
-              } else {
-                // the next SpMV reads other CTAs' rows of y: they must have finished this update
-                PM_SYNC_OR_FAIL();
-              }
-              if (tid == 0) {
-                c.hn = sqrt(fmax(c.hn, 0.0));
-                s.H[(j + 1) * PM_MAXM + j] = c.hn;
               }
             }
             if (tid == 0) {
