@@ -529,7 +529,29 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
   const int qa = min(b, (a + 3) & ~3);
   const int qb = max(qa, b & ~3);
   if (a + lane < qa) { E::dot(z1, v[a + lane], z[a + lane]); E::dot(w1, v[a + lane], w[a + lane]); }
-  int e = qa + 4 * lane;
+  int e = qa;
+  if constexpr (sizeof(S) == 8) {
+    // lane owns elements 2l, 2l+1 and 64+2l, 65+2l of each 128-element block: every
+    // 16-byte load instruction of a warp covers 512 contiguous bytes
+    auto ld2 = [](const S* p, S& x0, S& x1) {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      S t0, t1;
+      memcpy(&t0, &q.x, 8);
+      memcpy(&t1, &q.z, 8);
+      x0 = t0;
+      x1 = t1;
+    };
+    for (; e + 127 < qb; e += 128) {
+      S va, vb, vc, vd, za, zb, zc, zd, wa, wb, wc, wd;
+      const int p0 = e + 2 * lane, p1 = p0 + 64;
+      ld2(v + p0, va, vb); ld2(v + p1, vc, vd);
+      ld2(z + p0, za, zb); ld2(z + p1, zc, zd);
+      ld2(w + p0, wa, wb); ld2(w + p1, wc, wd);
+      E::dot(z0, va, za); E::dot(z1, vb, zb); E::dot(z0, vc, zc); E::dot(z1, vd, zd);
+      E::dot(w0, va, wa); E::dot(w1, vb, wb); E::dot(w0, vc, wc); E::dot(w1, vd, wd);
+    }
+  }
+  e += 4 * lane;
   for (; e + 128 + 3 < qb; e += 256) {        // two quads of each operand per lane in flight
     Quad<S> v0, v1, z0q, z1q, w0q, w1q;
     v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
@@ -1359,28 +1381,21 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             }
             // columns j-1 (second pass, subdiagonal nu) and j (first pass) of H, row l by
             // thread l; H is next read after later barriers, so the update starts at once
-            {
-              // one warp per row l, lanes splitting the sum (short FP64 dependency chains)
-              const int warp = tid >> 5, lane = tid & 31;
-              for (int l = warp; l <= j; l += PM_WARPS) {
-                if (l < j) {
-                  double g = 0.0;                // (H a)_l over the Hessenberg columns l-1 .. j-2
-                  for (int i = max(l - 1, 0) + lane; i < j - 1; i += 32) g = fma(s.H[l * PM_MAXM + i], s.h1[i], g);
-                  g = pm_warp_sum(g);
-                  if (lane == 0) {
-                    double hl = s.H[l * PM_MAXM + j - 1];
-                    if (!zfinal) {
-                      hl += s.h1[l];
-                      s.H[l * PM_MAXM + j - 1] = hl;
-                    }
-                    g = fma(hl, s.h1[j - 1], g);
-                    s.H[l * PM_MAXM + j] = (s.hb[l] - g) * c.inv;
-                  }
-                } else if (lane == 0) {
-                  if (j > 0 && !zfinal) s.H[j * PM_MAXM + j - 1] = c.hn;
-                  const double g = (j > 0) ? c.hn * s.h1[j - 1] : 0.0;
-                  s.H[j * PM_MAXM + j] = (c.dcoef - g) * c.inv;
+            for (int l = tid; l <= j; l += nth) {
+              if (l < j) {
+                double g = 0.0;
+                for (int i = max(l - 1, 0); i < j - 1; ++i) g = fma(s.H[l * PM_MAXM + i], s.h1[i], g);
+                double hl = s.H[l * PM_MAXM + j - 1];
+                if (!zfinal) {
+                  hl += s.h1[l];
+                  s.H[l * PM_MAXM + j - 1] = hl;
                 }
+                g = fma(hl, s.h1[j - 1], g);
+                s.H[l * PM_MAXM + j] = (s.hb[l] - g) * c.inv;
+              } else {
+                if (j > 0 && !zfinal) s.H[j * PM_MAXM + j - 1] = c.hn;
+                const double g = (j > 0) ? c.hn * s.h1[j - 1] : 0.0;
+                s.H[j * PM_MAXM + j] = (c.dcoef - g) * c.inv;
               }
             }
             update_rows2<S>(V, ld, j, ca, cb, E::coef(c.dcoef), scal_inv<S>(c), zp, Wv,
