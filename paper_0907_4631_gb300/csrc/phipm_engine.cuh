@@ -515,11 +515,13 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
   }
 }
 
-// Two dot products per left vector in one pass, for the lagged Gram-Schmidt step:
+// Two dot products per left vector in one pass, for the lagged Gram-Schmidt step
+// (WIDE: more loads in flight per lane, measured faster when one CTA streams a whole
+// problem and slower for the short runs of a grid team):
 // with L_i = V_i (i < nv) and L_nv = z, s.coef[i] = L_i . z and
 // s.coef[nv + 1 + i] = L_i . w (i <= nv).  Runs per warp as in dots_cta; each
 // segment leaves two warp-reduced partials in s.dred (even / odd slots).
-template <class S>
+template <class S, bool WIDE>
 __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* __restrict__ z,
                                              const S* __restrict__ w, int a, int b, double& dz, double& dw) {
   typedef Elem<S> E;
@@ -541,6 +543,18 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
       x0 = t0;
       x1 = t1;
     };
+    for (; WIDE && e + 255 < qb; e += 256) {    // one CTA per problem: two blocks in flight
+      S va, vb, vc, vd, za, zb, zc, zd, wa, wb, wc, wd;
+      S xa, xb, xc, xd, ya, yb, yc, yd, ua, ub, uc, ud;
+      const int p0 = e + 2 * lane, p1 = p0 + 64, p2 = p0 + 128, p3 = p0 + 192;
+      ld2(v + p0, va, vb); ld2(v + p1, vc, vd); ld2(v + p2, xa, xb); ld2(v + p3, xc, xd);
+      ld2(z + p0, za, zb); ld2(z + p1, zc, zd); ld2(z + p2, ya, yb); ld2(z + p3, yc, yd);
+      ld2(w + p0, wa, wb); ld2(w + p1, wc, wd); ld2(w + p2, ua, ub); ld2(w + p3, uc, ud);
+      E::dot(z0, va, za); E::dot(z1, vb, zb); E::dot(z0, vc, zc); E::dot(z1, vd, zd);
+      E::dot(w0, va, wa); E::dot(w1, vb, wb); E::dot(w0, vc, wc); E::dot(w1, vd, wd);
+      E::dot(z0, xa, ya); E::dot(z1, xb, yb); E::dot(z0, xc, yc); E::dot(z1, xd, yd);
+      E::dot(w0, xa, ua); E::dot(w1, xb, ub); E::dot(w0, xc, uc); E::dot(w1, xd, ud);
+    }
     for (; e + 127 < qb; e += 128) {
       S va, vb, vc, vd, za, zb, zc, zd, wa, wb, wc, wd;
       const int p0 = e + 2 * lane, p1 = p0 + 64;
@@ -575,7 +589,7 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
   dw = E::val(w0) + E::val(w1);
 }
 
-template <class S>
+template <class S, bool WIDE>
 __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -598,7 +612,7 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
       const long long r1 = min(rows, r0 + (fend - f));
       const S* v = (i < nv) ? V + (size_t)i * ld : z;
       double dz, dw;
-      dot_segment2<S>(v, z, w, lo + (int)r0, lo + (int)r1, dz, dw);
+      dot_segment2<S, WIDE>(v, z, w, lo + (int)r0, lo + (int)r1, dz, dw);
       dz = pm_warp_sum(dz);
       dw = pm_warp_sum(dw);
       if (lane == 0) {
@@ -1304,7 +1318,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             kry_steps += 1;
             gs_vectors += j;
             __syncthreads();
-            dots2_cta<S>(V, ld, j, zp, Wv, lo, hi, s);
+            dots2_cta<S, !Team::multi>(V, ld, j, zp, Wv, lo, hi, s);
             PM_SUM_OR_FAIL(2 * (j + 1));
             // scalars by one warp (||a||^2, a.b); a and b copied by every thread
             if (tid < 32) {
