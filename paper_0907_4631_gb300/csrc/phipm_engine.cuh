@@ -5,6 +5,7 @@
 // cost model) on bit-identical inputs, so all CTAs take the same decisions
 // without a broadcast.
 #pragma once
+#include <type_traits>
 #include "phipm_common.cuh"
 #include "phipm_mlp.cuh"
 
@@ -259,6 +260,102 @@ __device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
       if (iz < A.nz - 1) f2_add_prod(acc, A.cp2[2], x(r + pl));
     }
     return f2_round(acc);
+  }
+}
+
+// Two CSR rows r and r2 (r2 < 0: none) at once: both rows' extents, then up to
+// PM_CSR_U column indices and values of each, then the matching x entries, so that the
+// three dependent loads of a row (extent, index, x) overlap with the other row's and
+// every load of one level is in flight together.  Short rows (the 5-point operators)
+// take one round.  Arithmetic as in spmv_row.
+#define PM_CSR_U 6
+template <class S, class XL>
+__device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, const XL& x, S& y0, S& y1) {
+  typedef Elem<S> E;
+  constexpr int kind = E::kind;
+  typedef typename std::conditional<kind == 0, double, typename std::conditional<kind == 1, float, F2Acc>::type>::type
+      Acc;
+  typedef typename std::conditional<kind == 0, double, typename std::conditional<kind == 1, float, df32>::type>::type
+      Val;
+  Acc c0, c1;
+  if constexpr (kind == 2) { c0 = f2_zero(); c1 = f2_zero(); }
+  else { c0 = 0; c1 = 0; }
+  const int a0 = __ldg(&A.rowptr[r]), b0 = __ldg(&A.rowptr[r + 1]);
+  int a1 = 0, b1 = 0;
+  if (r2 >= 0) {
+    a1 = __ldg(&A.rowptr[r2]);
+    b1 = __ldg(&A.rowptr[r2 + 1]);
+  }
+  const int len = max(b0 - a0, b1 - a1);
+  for (int t = 0; t < len; t += PM_CSR_U) {
+    int col0[PM_CSR_U], col1[PM_CSR_U];
+    Val v0[PM_CSR_U], v1[PM_CSR_U];
+#pragma unroll
+    for (int u = 0; u < PM_CSR_U; ++u) {
+      const int k0 = a0 + t + u, k1 = a1 + t + u;
+      col0[u] = (k0 < b0) ? __ldg(&A.colind[k0]) : -1;
+      col1[u] = (k1 < b1) ? __ldg(&A.colind[k1]) : -1;
+      if constexpr (kind == 0) {
+        v0[u] = (k0 < b0) ? __ldg(&A.val[k0]) : 0.0;
+        v1[u] = (k1 < b1) ? __ldg(&A.val[k1]) : 0.0;
+      } else if constexpr (kind == 1) {
+        v0[u] = (k0 < b0) ? __ldg(&A.valf[k0]) : 0.f;
+        v1[u] = (k1 < b1) ? __ldg(&A.valf[k1]) : 0.f;
+      } else {
+        const float2 q0 = (k0 < b0) ? __ldg(reinterpret_cast<const float2*>(&A.val2[k0])) : make_float2(0.f, 0.f);
+        const float2 q1 = (k1 < b1) ? __ldg(reinterpret_cast<const float2*>(&A.val2[k1])) : make_float2(0.f, 0.f);
+        v0[u].hi = q0.x; v0[u].lo = q0.y;
+        v1[u].hi = q1.x; v1[u].lo = q1.y;
+      }
+    }
+    S x0[PM_CSR_U], x1[PM_CSR_U];
+#pragma unroll
+    for (int u = 0; u < PM_CSR_U; ++u) {
+      x0[u] = (col0[u] >= 0) ? x(col0[u]) : E::from_d(0.0);
+      x1[u] = (col1[u] >= 0) ? x(col1[u]) : E::from_d(0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < PM_CSR_U; ++u) {
+      if (col0[u] >= 0) {
+        if constexpr (kind == 0) c0 = fma(v0[u], x0[u], c0);
+        else if constexpr (kind == 1) c0 = fmaf(v0[u], x0[u], c0);
+        else f2_add_prod(c0, v0[u], x0[u]);
+      }
+      if (col1[u] >= 0) {
+        if constexpr (kind == 0) c1 = fma(v1[u], x1[u], c1);
+        else if constexpr (kind == 1) c1 = fmaf(v1[u], x1[u], c1);
+        else f2_add_prod(c1, v1[u], x1[u]);
+      }
+    }
+  }
+  if constexpr (kind == 2) {
+    y0 = f2_round(c0);
+    y1 = f2_round(c1);
+  } else {
+    y0 = c0;
+    y1 = c1;
+  }
+}
+
+// out[r] = (A x)[r] * sc over this CTA's rows (CSR rows two at a time per thread)
+template <class S, class XL>
+__device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __restrict__ out,
+                                          typename Elem<S>::Coef sc, bool scale, int lo, int hi) {
+  typedef Elem<S> E;
+  const int nth = blockDim.x;
+  if (A.kind == 0) {
+    for (int r = lo + threadIdx.x; r < hi; r += 2 * nth) {
+      const int r2 = (r + nth < hi) ? r + nth : -1;
+      S y0, y1;
+      spmv_csr_pair<S>(A, r, r2, x, y0, y1);
+      out[r] = scale ? E::scale(y0, sc) : y0;
+      if (r2 >= 0) out[r2] = scale ? E::scale(y1, sc) : y1;
+    }
+  } else {
+    for (int r = lo + threadIdx.x; r < hi; r += nth) {
+      const S y = spmv_row<S>(A, r, x);
+      out[r] = scale ? E::scale(y, sc) : y;
+    }
   }
 }
 
@@ -1306,13 +1403,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             if (j == 0) {
               const C sc = scal_inv<S>(c);   // 1/beta
               DLoadAs<S, Team::multi> xl{wp, lo, hi};
-              for (int r = lo + tid; r < hi; r += nth) {
-                V[r] = E::from_d(wp[r] * c.inv);
-                Wv[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
-              }
+              for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
+              spmv_rows<S>(P.A, xl, Wv, sc, true, lo, hi);
             } else {
               VecLoad<S, Team::multi> xl{zp, lo, hi};
-              for (int r = lo + tid; r < hi; r += nth) Wv[r] = spmv_row<S>(P.A, r, xl);
+              spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi);
             }
             matvecs += 1;
             kry_steps += 1;
