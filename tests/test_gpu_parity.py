@@ -201,3 +201,27 @@ def test_pair_mode_agrees_with_native_fp64():
     u2, st2 = _gpu(_solver("f64pair"), pr)
     assert _rel(u2, u64) <= 1e-9
     assert st64["steps"] == st2["steps"] and st64["krylov_steps"] == st2["krylov_steps"]
+
+
+@pytest.mark.parametrize("n,prec,team", [(6000, "f64", 1), (6000, "f64", 152), (6000, "f64pair", 8),
+                                         (6000, "f32", 4), (6, "f64", 1), (6, "f64pair", 1), (9, "f32", 1),
+                                         (4, "f64", 1), (4, "f64pair", 1)])
+def test_arnoldi_breakdown_three_eigenvalues(n, prec, team):
+    """A diagonal operator with three distinct eigenvalues solved as nonsymmetric
+    (Arnoldi): the Krylov space is invariant after three steps, so the fourth candidate
+    is rounding noise.  With n = 4 most of that noise lies in the span of the basis: the
+    candidate fails the Pythagorean orthogonality check and is projected a second time.  In IEEE
+    FP64 the noise falls below the breakdown threshold (R12) and the space stops at
+    dimension 3; with float pairs (48-bit basis) or FP32 it can stay above it and the
+    solve goes on with directions whose coupling to the problem is at the noise level.
+    Teams of 1 to 152 CTAs.  Truth: the scalar phi functions."""
+    lams = np.array([-1.0, -5.0, -20.0])[np.arange(n) % 3]
+    A = wl.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), lams.copy())
+    b = [wl.normal(77, k, n) for k in range(3)]
+    s = pm.Phipm(prec)
+    s.set_team(team)
+    u, st, _ = s.solve(0.7, pm.DeviceOperator(A), _dev(b), 1e-9, 0)
+    ref = T.solution_diagonal(lams, b, 0.7)
+    assert _rel(u.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
+    if prec == "f64":
+        assert st["krylov_steps"] <= 4 * max(1, st["expms"])    # the space never grows past dimension 3
