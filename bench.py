@@ -93,6 +93,21 @@ def measured_peaks():
         return PEAK_FALLBACK, "fallback"
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (replicas: whole-job throughput is bounded by it)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_rank in total_ms."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
 def algorithmic_bytes(pr, stats, precision) -> float:
     """SpMV + Arnoldi bytes of one solve (per-step model).
 
@@ -383,12 +398,8 @@ def run_batched(args, world, rank, local):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * count * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
+    value = replica_throughput(count * args.steps, world, total_ms)
     kernel_ms = stats[0]["kernel_ms"]
     u_gpu = [u.cpu().numpy() for u in pk.outs]
 
@@ -396,12 +407,8 @@ def run_batched(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         et = time_batch(batch, stream, flush, args.steps, packed=pk)
-        tot = sum(et)
-        if dist:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": world * count * args.steps / (tot / 1e3), "unit": "solves/s",
+        tot = max_over_ranks(sum(et), dist, "cuda")
+        e2e = {"value": replica_throughput(count * args.steps, world, tot), "unit": "solves/s",
                "h2d_bytes_per_step": int(pk.in_bytes), "d2h_bytes_per_step": int(pk.out_bytes)}
 
     # the plain FP64 GPU solver, one problem per call, on an evenly spaced sample
@@ -611,12 +618,8 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
+    value = replica_throughput(args.steps, world, total_ms)
     u_gpu = u.cpu().numpy()
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -645,12 +648,8 @@ def main():
             e1.record(stream)
             e1.synchronize()
             et.append(e0.elapsed_time(e1))
-        tot = sum(et)
-        if dist:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": world * args.steps / (tot / 1e3), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+        tot = max_over_ranks(sum(et), dist, "cuda")
+        e2e = {"value": replica_throughput(args.steps, world, tot), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     peak, peak_kind = measured_peaks()
