@@ -346,7 +346,7 @@ def run_batched(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    probs = make_batch(args.workload)
+    probs = make_batch(args.workload, 0, args.count if args.count > 0 else None)
     count = len(probs)
     solver = pm.Phipm(prec)
     stream = torch.cuda.current_stream()
@@ -557,6 +557,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default team size (no phipm_autotune)")
+    ap.add_argument("--count", type=int, default=0, help="batched workloads: only the first COUNT problems")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

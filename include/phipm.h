@@ -162,7 +162,10 @@ phipm_status phipm_solve_host(phipm_handle* h, double t_end, const phipm_operato
  * length count in host memory: t_end, A (CSR arrays device pointers), p, b
  * (b[i] is a host array of p[i]+1 device pointers), tol, symm, u (device
  * pointers).  stats and per_problem (host, may be NULL) receive one entry per
- * problem.  Returns PHIPM_OK only if every problem succeeded. */
+ * problem.  Returns PHIPM_OK only if every problem succeeded.  Problems are
+ * taken largest first by teams of one CTA or of a K-CTA thread-block cluster
+ * (see phipm_set_team); the launch sequence is captured once as a CUDA graph
+ * and replayed while sizes, buffers, parameters and team size are unchanged. */
 phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, const double* t_end,
                                  const phipm_operator* A, const int32_t* p,
                                  const double* const* const* b, const double* tol,
@@ -290,7 +293,10 @@ phipm_status phipm_autotune(phipm_handle* h, double t_end, const phipm_operator*
                             const double* const* b, double tol, int32_t symm, double* u,
                             phipm_tune_entry* report, int32_t max_report, int32_t* n_report, void* stream);
 /* Force a team size for every later solve of this handle (0 = the tuned table or
- * the default; larger than the co-resident grid is clamped to it). */
+ * the default; larger than the co-resident grid is clamped to it).  For
+ * phipm_solve_batched the team is a thread-block cluster of up to 8 CTAs per
+ * problem (1 = one CTA per problem); by default the batch picks 1, 2 or 4 from
+ * the share of its largest problem in the total work. */
 phipm_status phipm_set_team(phipm_handle* h, int32_t team);
 /* The team size a solve of this shape would use now (0 for invalid arguments). */
 int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n);

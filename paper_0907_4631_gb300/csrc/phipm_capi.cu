@@ -66,6 +66,74 @@ k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams pr
   }
 }
 
+// Batched form with a team of K CTAs per problem: each thread-block cluster is one
+// team (rows split over its CTAs, reductions through per-cluster partials, barriers
+// on a counter in rank 0's shared memory) and pulls problems from the atomic queue.
+// Large problems of an uneven batch then get K SMs' bandwidth instead of one.
+__device__ __forceinline__ unsigned pm_cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned pm_cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned pm_cluster_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void pm_cluster_arrive_wait() {   // full cluster barrier (hardware)
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+template <class T>
+__device__ __forceinline__ T* pm_map_rank(T* p, unsigned rank) {   // generic address of p in CTA rank's smem
+  T* q;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(q) : "l"(p), "r"(rank));
+  return q;
+}
+
+template <class S>
+__global__ void __launch_bounds__(PM_THREADS, 1)
+k_solve_cluster(const DevProblem* probs, const int* order, int count, DevParams prm, DevResult* res,
+                unsigned char* slots, SlotLayout lay, int* queue, double* partials, int* err) {
+  extern __shared__ __align__(16) unsigned char pm_smem[];
+  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
+  __shared__ unsigned long long s_bar;
+  __shared__ int s_next;
+  const unsigned rank = pm_cluster_rank(), K = pm_cluster_size(), cid = pm_cluster_id();
+  if (threadIdx.x == 0) {
+    s_bar = 0;
+    s_next = 0;
+  }
+  pm_cluster_arrive_wait();            // every CTA's counter initialised before remote use
+  ClusterTeam team{pm_map_rank(&s_bar, 0), err, prm.timeout_cycles, (int)rank, (int)K, 0ull};
+  const int* next0 = pm_map_rank(&s_next, 0);
+  unsigned char* base = slots + (size_t)cid * lay.bytes;
+  PmWork w{partials + (size_t)cid * 2 * K * PM_PSTRIDE, (double*)(base + lay.e_off)};
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+    if (!team.sync()) break;
+    const int q = *((volatile const int*)next0);
+    if (!team.sync()) break;           // read before rank 0 takes the next problem
+    if (q >= count) break;
+    const int id = order[q];
+    DevProblem P = probs[id];
+    P.V = base + lay.v_off;
+    P.W = (double*)(base + lay.w_off);
+    P.Y = base + lay.y_off;
+    P.ld = lay.ld;
+    phipm_device<ClusterTeam, S>(team, P, prm, res[id], s, w);
+    if (rank == 0 && threadIdx.x == 0) {
+      const int e = *((volatile int*)err);
+      if (e != 0 && res[id].status == PM_OK) res[id].status = e;
+    }
+  }
+  pm_cluster_arrive_wait();            // no CTA leaves while others may still read rank 0's memory
+}
+
 // CSR values converted for the FP32 basis (valf) or the float-pair basis (val2);
 // blockIdx.y selects the problem, blockIdx.x strides over its values.
 __global__ void k_convert_values(const DevProblem* probs, int count, int mode) {
@@ -192,7 +260,51 @@ template <class S>
 static cudaError_t setup_kernels(int smem) {
   cudaError_t e = cudaFuncSetAttribute(k_solve_grid<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_solve_cluster<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_solve_queue<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// Cluster launch of the batched form: K CTAs per team, `clusters` teams.
+template <class S>
+static cudaError_t launch_cluster(int K, int clusters, cudaStream_t stream, const DevProblem* probs, const int* order,
+                                  int count, const DevParams& prm, DevResult* res, unsigned char* slots,
+                                  const SlotLayout& lay, int* queue, double* partials, int* err) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * K));
+  cfg.blockDim = dim3(PM_THREADS);
+  cfg.dynamicSmemBytes = sizeof(PmShared);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_solve_cluster<S>, probs, order, count, prm, res, slots, lay, queue, partials, err);
+}
+
+// Co-resident clusters of K CTAs (0 when the GPU cannot hold one).
+template <class S>
+static int cluster_capacity(int K) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)K);
+  cfg.blockDim = dim3(PM_THREADS);
+  cfg.dynamicSmemBytes = sizeof(PmShared);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)K;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_solve_cluster<S>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* params) {
@@ -729,7 +841,36 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
   const SlotLayout lay = slot_layout(nmax, pmax, h->params.m_max, es);
-  const int slots = std::max(1, std::min(count, queue_occupancy(prec) * h->num_sms));
+  // Team per problem: one CTA (queue) or a cluster of K CTAs.  phipm_set_team forces K
+  // (up to 8); otherwise K grows with the share of the largest problem in the batch's
+  // work: with ratio = SMs x largest cost / total cost, K = 1 below 0.5 (many similar
+  // problems keep every SM busy), 2 below 1, else 4 (measured on the 256-problem
+  // uneven batch: K = 1, 2, 4, 8 give 471, 805, 1140, 946 solves/s; on 1024 equal
+  // problems K = 1 is fastest).
+  int K;
+  if (h->team_force > 0) {
+    K = std::min(h->team_force, 8);
+  } else {
+    double cmax = 0.0, csum = 0.0;
+    for (int i = 0; i < count; ++i) {
+      cmax = std::max(cmax, cost[i]);
+      csum += cost[i];
+    }
+    const double ratio = csum > 0.0 ? h->num_sms * cmax / csum : 0.0;
+    K = ratio < 0.5 ? 1 : ratio < 1.0 ? 2 : 4;
+  }
+  int clusters = 0;
+  if (K >= 2) {
+    clusters = prec == PHIPM_F32_MIXED ? cluster_capacity<float>(K)
+               : prec == PHIPM_F64_PAIR ? cluster_capacity<df32>(K)
+                                        : cluster_capacity<double>(K);
+    if (clusters < 1) K = 1;
+  }
+  if (K < 2) K = 1;
+  const int slots = K >= 2 ? std::max(1, std::min(count, clusters))
+                           : std::max(1, std::min(count, queue_occupancy(prec) * h->num_sms));
+  if (K >= 2 && !h->partials.ensure((size_t)slots * 2 * K * PM_PSTRIDE * sizeof(double)))
+    return fail(h, PHIPM_ENOMEM, "partials");
   if (!h->ws.ensure((size_t)lay.bytes * slots)) return fail(h, PHIPM_ENOMEM, "workspace");
   const size_t pb = sizeof(DevProblem) * count, ob = sizeof(int) * count, rb = sizeof(DevResult) * count;
   if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(pb + ob) ||
@@ -757,6 +898,9 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   put(ptrs, sizeof(ptrs));
   put(&count, sizeof(count));
   put(&slots, sizeof(slots));
+  put(&K, sizeof(K));
+  const void* pp = h->partials.p;
+  put(&pp, sizeof(pp));
   put(&lay, sizeof(lay));
   put(&prec, sizeof(prec));
   put(&convert, sizeof(convert));
@@ -776,8 +920,21 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
     if (convert)
       k_convert_values<<<dim3(conv_blocks(max_nnz) / 8 + 1, count), 256, 0, gs>>>((const DevProblem*)h->probs.p,
                                                                                  count, prec);
-    launch_queue_any(prec, slots, gs, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
-                     (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+    if (K >= 2) {
+      int* err = (int*)((char*)h->sync.p + 1024);
+      cudaMemsetAsync(err, 0, sizeof(int), gs);
+      const DevProblem* pd = (const DevProblem*)h->probs.p;
+      const int* od = (const int*)h->order.p;
+      DevResult* rd = (DevResult*)h->res.p;
+      unsigned char* ws = (unsigned char*)h->ws.p;
+      double* pt = (double*)h->partials.p;
+      if (prec == PHIPM_F32_MIXED) launch_cluster<float>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
+      else if (prec == PHIPM_F64_PAIR) launch_cluster<df32>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
+      else launch_cluster<double>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
+    } else {
+      launch_queue_any(prec, slots, gs, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
+                       (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
+    }
     cudaMemcpyAsync(h->res_host.p, h->res.p, rb, cudaMemcpyDeviceToHost, gs);
     fetch_trace_count(h, prm, gs);
     e = cudaStreamEndCapture(h->gstream, &graph);

@@ -144,6 +144,56 @@ struct CtaTeam {
   static constexpr bool multi = false;
 };
 
+// Barrier over the K CTAs of a thread-block cluster: the same counting protocol as
+// pm_grid_barrier on a 64-bit counter in rank 0's shared memory, reached through
+// distributed shared memory with cluster-scope acquire / release (no L2 round trip),
+// bounded by timeout cycles and the launch's error word.
+__device__ __forceinline__ unsigned long long pm_atom_add_cluster(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.cluster.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long pm_ld_acquire_cluster(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.cluster.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool pm_cluster_barrier(unsigned long long* cnt, int K, int* err, long long timeout,
+                                                   unsigned long long& gen) {
+  __syncthreads();
+  __shared__ int s_cfail;
+  if (threadIdx.x == 0) {
+    s_cfail = 0;
+    gen += 1;
+    const unsigned long long target = gen * (unsigned long long)K;
+    const unsigned long long prev = pm_atom_add_cluster(cnt, 1ull);
+    if (prev + 1 < target) {
+      const long long t0 = clock64();
+      for (unsigned it = 1; pm_ld_acquire_cluster(cnt) < target; ++it) {
+        if ((it & 15u) == 0) {
+          if (*((volatile int*)err) != 0) { s_cfail = 1; break; }
+          if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_cfail = 1; break; }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return s_cfail == 0;
+}
+
+// A team of the K CTAs of one cluster (batched form: one problem per cluster).
+struct ClusterTeam {
+  unsigned long long* bar;               // rank 0's arrival counter (distributed shared memory)
+  int* err;
+  long long timeout;
+  int r, k;
+  mutable unsigned long long gen = 0;
+  __device__ int rank() const { return r; }
+  __device__ int size() const { return k; }
+  __device__ bool sync() const { return pm_cluster_barrier(bar, k, err, timeout, gen); }
+  static constexpr bool multi = true;
+};
+
 // ------------------------------------------------------------------------------------
 // reductions
 // ------------------------------------------------------------------------------------

@@ -225,3 +225,24 @@ def test_arnoldi_breakdown_three_eigenvalues(n, prec, team):
     assert _rel(u.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
     if prec == "f64":
         assert st["krylov_steps"] <= 4 * max(1, st["expms"])    # the space never grows past dimension 3
+
+
+@pytest.mark.parametrize("prec,K", [("f64pair", 2), ("f64pair", 4), ("f64", 8), ("f32", 4)])
+def test_batched_cluster_teams(prec, K):
+    """Batched form with a thread-block cluster of K CTAs per problem (rows split over the
+    cluster, barriers in distributed shared memory): every result matches the oracle,
+    including problems too small to give each CTA of the cluster rows."""
+    probs = wl.batched_convdiff_problems(count=9, side_lo=6, side_hi=72, seed0=4950)
+    if prec == "f32":
+        for p_ in probs:
+            p_.tol = 1e-5
+    s = pm.Phipm(prec)
+    s.set_team(K)
+    ops = [pm.DeviceOperator(p_.op) for p_ in probs]
+    us, stats, sts = s.solve_batched([p_.t_end for p_ in probs], ops, [_dev(p_.b) for p_ in probs],
+                                     [p_.tol for p_ in probs], [0] * len(probs))
+    torch.cuda.synchronize()
+    assert all(x == pm.OK for x in sts)
+    for p_, u in zip(probs, us):
+        ref, _ = O.phipm(p_.t_end, p_.op, p_.b, p_.tol, 0)
+        assert _rel(u.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
