@@ -664,7 +664,16 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
   const bool convert = prec != PHIPM_F64 && any_csr(&P, 1);
   const int team = team_req > 0 ? std::min(team_req, h->grid_blocks[prec]) : choose_team(h, prec, A->kind, n);
 
-  if (team >= 2) {
+  // teams of 2..8 CTAs run as one thread-block cluster (barriers in distributed shared
+  // memory); larger teams as a cooperative grid
+  int cK = 0;
+  if (team >= 2 && team <= 8) {
+    cK = prec == PHIPM_F32_MIXED ? cluster_capacity<float>(team)
+         : prec == PHIPM_F64_PAIR ? cluster_capacity<df32>(team)
+                                  : cluster_capacity<double>(team);
+    cK = cK >= 1 ? team : 0;
+  }
+  if (team >= 2 && cK == 0) {
     const long long ld = round_ld(n);
     const size_t vbytes = (size_t)M1 * ld * es, wbytes = (size_t)(p + 1) * ld * 8, ybytes = 2 * (size_t)ld * es;
     if (!h->ws.ensure(vbytes + wbytes + ybytes)) return fail(h, PHIPM_ENOMEM, "workspace");
@@ -715,9 +724,25 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
       k_convert_values<<<dim3(conv_blocks(P.A.nnz), 1), 256, 0, stream>>>((const DevProblem*)h->probs.p, 1, prec);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "value conversion");
     }
+    if (cK >= 2) {
+      if (!h->partials.ensure((size_t)2 * cK * PM_PSTRIDE * sizeof(double))) return fail(h, PHIPM_ENOMEM, "partials");
+      int* err = (int*)((char*)h->sync.p + 1024);
+      if ((e = cudaMemsetAsync(err, 0, sizeof(int), stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
+    }
     cudaEventRecord(h->ev0, stream);
-    e = launch_queue_any(prec, 1, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm, res_d,
-                         (unsigned char*)h->ws.p, lay, queue);
+    if (cK >= 2) {
+      const DevProblem* pd = (const DevProblem*)h->probs.p;
+      const int* od = (const int*)h->order.p;
+      unsigned char* ws = (unsigned char*)h->ws.p;
+      double* pt = (double*)h->partials.p;
+      int* err = (int*)((char*)h->sync.p + 1024);
+      if (prec == PHIPM_F32_MIXED) e = launch_cluster<float>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
+      else if (prec == PHIPM_F64_PAIR) e = launch_cluster<df32>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
+      else e = launch_cluster<double>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
+    } else {
+      e = launch_queue_any(prec, 1, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm, res_d,
+                           (unsigned char*)h->ws.p, lay, queue);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "launch");
     cudaEventRecord(h->ev1, stream);
   }
