@@ -246,3 +246,37 @@ def test_batched_cluster_teams(prec, K):
     for p_, u in zip(probs, us):
         ref, _ = O.phipm(p_.t_end, p_.op, p_.b, p_.tol, 0)
         assert _rel(u.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
+
+
+def test_batched_graph_replay_sees_new_inputs():
+    """The batched launch sequence is captured once and replayed: a second call with the same
+    shapes but new right-hand sides, new t_end and new tolerances (descriptors re-read from
+    pinned host memory, vectors read from device memory) must give the new answers, and a
+    new team size on the same handle (a different launch) must not reuse the graph."""
+    s = pm.Phipm("f64pair")
+    probs = wl.batched_convdiff_problems(count=5, side_lo=16, side_hi=40, seed0=4970)
+    ops = [pm.DeviceOperator(p_.op) for p_ in probs]
+    bs = [_dev(p_.b) for p_ in probs]
+    batch = s.batch([p_.t_end for p_ in probs], ops, bs, [p_.tol for p_ in probs], [0] * len(probs))
+    batch.run()
+    first = [u.cpu().numpy().copy() for u in batch.outs]
+    for p_, u in zip(probs, first):
+        ref, _ = O.phipm(p_.t_end, p_.op, p_.b, p_.tol, 0)
+        assert _rel(u, ref) <= TOL64
+    # same shapes, new values: b scaled in place on the device, new t_end and tol through a new call
+    for b in bs:
+        for x in b:
+            x.mul_(-0.5)
+    t2 = [0.5 * p_.t_end for p_ in probs]
+    tol2 = [1e-9] * len(probs)
+    us, st, sts = s.solve_batched(t2, ops, bs, tol2, [0] * len(probs), outs=batch.outs)
+    torch.cuda.synchronize()
+    for p_, u, t, tl in zip(probs, us, t2, tol2):
+        ref, _ = O.phipm(t, p_.op, [-0.5 * x for x in p_.b], tl, 0)
+        assert _rel(u.cpu().numpy(), ref) <= TOL64
+    s.set_team(2)                                      # cluster teams: a new graph
+    us, st, sts = s.solve_batched(t2, ops, bs, tol2, [0] * len(probs))
+    torch.cuda.synchronize()
+    for p_, u, t, tl in zip(probs, us, t2, tol2):
+        ref, _ = O.phipm(t, p_.op, [-0.5 * x for x in p_.b], tl, 0)
+        assert _rel(u.cpu().numpy(), ref) <= TOL64
