@@ -9,9 +9,9 @@ int32, p = 4, b_k ~ N(0,1) (seeded), t_end = 1e-3, Tol = 1e-8.
              CUDA events, L2 flushed (256 MiB write) between timed solves
   e2e        the same through phipm_solve_host: H2D of A and b from pinned host
              memory, the solve, D2H of u, every step
-  roofline   the solver kernel's algorithmic HBM bytes (SpMV + Arnoldi/CGS2
-             per-step model) / its event-timed duration, against the measured
-             copy bandwidth
+  roofline   the solver kernel's algorithmic bytes (SpMV + Arnoldi per-step
+             model: two passes over the basis per step) / its event-timed
+             duration, against the measured copy bandwidth
   cpu_baseline  the FP64 CPU oracle (as it stands) timed on the host, one
              full solve of the same seeded inputs; its result also checks parity
 

@@ -92,10 +92,11 @@ typedef struct {
 /* stats(1..4) of Sec. 3.5 plus the sum of accepted error estimates.
  * matvecs counts the products with A actually performed (the basis is reused
  * when only tau changes and extended when m grows).  krylov_steps counts
- * Arnoldi/Lanczos steps; gs_vectors sums, over classical Gram-Schmidt steps,
- * the number of basis vectors each projection pass touched (j+1 at step j;
- * 0 for Lanczos steps).  kernel_ms is the device time of the solver kernel,
- * from CUDA events on the call's stream. */
+ * Arnoldi/Lanczos steps; gs_vectors sums, over the Arnoldi steps (and the
+ * completion of each extension's last vector), the number of earlier basis
+ * vectors each orthogonalisation pass reads (j at step j; 0 for Lanczos steps).
+ * kernel_ms is the device time of the solver kernel, from CUDA events on the
+ * call's stream. */
 typedef struct {
   int64_t steps;
   int64_t rejects;

@@ -30,13 +30,40 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and blank-line runs, so that the hash of a kernel
+    build does not change with its comments (string literals keep their contents)."""
+    import re
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    code = "".join(out)
+    return "\n".join(l.rstrip() for l in code.splitlines() if l.strip())
+
+
 def source_hash() -> str:
-    """sha256 of the CUDA sources and the ABI header (identifies a kernel build)."""
+    """sha256 of the CUDA sources and the ABI header with comments stripped (identifies
+    the code of a kernel build)."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(SOURCES + HEADERS):
-        h.update(open(os.path.join(CSRC, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "phipm.h"), "rb").read())
+        h.update(_code_only(open(os.path.join(CSRC, f)).read()).encode())
+    h.update(_code_only(open(os.path.join(ROOT, "include", "phipm.h")).read()).encode())
     return h.hexdigest()[:16]
 
 

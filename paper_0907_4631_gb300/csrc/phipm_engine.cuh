@@ -1254,7 +1254,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     c.normb = normb;
     c.symmetric = symmetric ? 1 : 0;
     // Lanczos (Algorithm 2) for symmetric A with an FP64-class basis; the FP32
-    // basis always uses full CGS2 (the three-term recurrence loses orthogonality)
+    // basis always uses full Arnoldi orthogonalisation (the three-term recurrence
+    // loses orthogonality in FP32)
     c.lanczos = (symmetric && E::kind != 1) ? 1 : 0;
     c.go = (n > 0 && normb > 0.0) ? 1 : 0;
     c.tol = P.tol > 0.0 ? P.tol : 1e-7;

@@ -80,3 +80,14 @@ def test_tuning_entry_points_reject_null_handles(tmp_path):
     assert L.phipm_tune_load(None, path) == pm.EINVAL
     assert L.phipm_set_team(None, 4) == pm.EINVAL
     assert L.phipm_team_for(None, pm.F64, 0, 1000) == 0
+
+
+def test_source_hash_ignores_comments_only():
+    """The build hash keys stored profiler counters to kernel code: a comment edit must
+    leave it unchanged, a code edit must change it, and string literals stay intact."""
+    from paper_0907_4631_gb300 import build
+    base = 'int f(int a) {\n  return a + 1;  // one\n}\nconst char* s = "a // b";\n'
+    assert build._code_only(base) == build._code_only(base.replace("// one", "/* two\n */"))
+    assert build._code_only(base) != build._code_only(base.replace("a + 1", "a + 2"))
+    assert '"a // b"' in build._code_only(base)
+    assert len(build.source_hash()) == 16
