@@ -38,6 +38,12 @@ WORKLOADS = {
                            precision="f64pair"),
     "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64pair"),
     "laplacian3d_128": dict(metric_cfg="FP32-basis 128^3 Laplacian stencil, p=2, tol 1e-5", precision="f32"),
+    "heston_100x51": dict(metric_cfg="Heston PDE (Sec. 4.1), 100x51 grid, n 5100, u' = Au + b_1, T = 1, tol 1e-4",
+                          precision="f64pair"),
+    "ninepoint30_phi4": dict(metric_cfg="nine-point 30x30 matrix (n 900, nnz 7,744), sum of t^k phi_k(tA) 1, "
+                                        "k <= 4, t = 2, tol 2^-26 (Sec. 4.2, Experiment 2), phipm", precision="f64pair"),
+    "ninepoint30_phi4_phip": dict(metric_cfg="the same problem with the fixed-dimension variant phip (m = 30)",
+                                  precision="f64pair", params=dict(controller=2, m_init=30)),
     "batched_convdiff_256": dict(metric_cfg="256 independent convection-diffusion problems, sides U{64..256}, "
                                             "p U{1..4}, tol 1e-8, one persistent launch replayed as a CUDA graph",
                                  precision="f64pair", batched=True),
@@ -81,7 +87,19 @@ def make_problem(name: str):
         return wl.laplacian_2d_problem()
     if name == "laplacian3d_128":
         return wl.laplacian_3d_problem()
+    if name == "heston_100x51":
+        return wl.heston_problem()
+    if name.startswith("ninepoint30_phi4"):
+        return wl.nine_point_phi_sum_problem(30)
     raise ValueError(name)
+
+
+def oracle_params(name: str) -> dict:
+    """The oracle's parameters for a workload's controller (phip: adapt_m off, m = m_init)."""
+    prm = WORKLOADS[name].get("params", {})
+    if prm.get("controller") == 2:
+        return dict(adapt_m=False, m_init=prm.get("m_init", 10))
+    return {}
 
 
 def measured_peaks():
@@ -186,11 +204,11 @@ def run_oracle_subprocess(workload: str, horizon: float, save_u: str | None) -> 
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np
-from bench import make_problem
+from bench import make_problem, oracle_params
 from oracle import phipm_oracle as O
 pr = make_problem({workload!r})
 t0 = time.perf_counter()
-u, st = O.phipm(pr.t_end * {horizon!r}, pr.op, pr.b, pr.tol, pr.symm)
+u, st = O.phipm(pr.t_end * {horizon!r}, pr.op, pr.b, pr.tol, pr.symm, oracle_params({workload!r}))
 dt = time.perf_counter() - t0
 if {save_u!r}:
     np.save({save_u!r}, u)
@@ -584,7 +602,7 @@ def main():
 
     pr = make_problem(args.workload)
     spec = WORKLOADS[args.workload]
-    solver = pm.Phipm(spec["precision"])
+    solver = pm.Phipm(spec["precision"], **spec.get("params", {}))
     A = pm.DeviceOperator(pr.op)
     b = [torch.as_tensor(x).cuda() for x in pr.b]
     u = torch.empty(pr.n, dtype=torch.float64, device="cuda")

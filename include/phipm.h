@@ -121,9 +121,17 @@ typedef struct {
   int64_t max_steps;
   int64_t max_rejects;
   int32_t precision;      /* phipm_precision */
-  int32_t controller;     /* 0 = the paper's controller; 1 = learned proposal (see below) */
+  int32_t controller;     /* phipm_controller: 0 = the paper's controller; 1 = learned
+                             proposal (see below); 2 = fixed Krylov dimension (phip) */
   int64_t timeout_cycles; /* bound on every device-side spin-wait, in clock64 cycles */
 } phipm_params;
+
+/* Controllers.  PHIPM_CTRL_FIXED_M is the fixed-dimension variant the paper
+ * compares phipm with (phip, Sec. 4.2): the same algorithm with the m branch of
+ * Algorithm 3 never taken, so every attempt uses m = m_init (shortened only by a
+ * happy breakdown, as in phipm) and only tau adapts (Eq. taunew with the q
+ * estimate of Eq. 6). */
+typedef enum { PHIPM_CTRL_PAPER = 0, PHIPM_CTRL_LEARNED = 1, PHIPM_CTRL_FIXED_M = 2 } phipm_controller;
 
 #define PHIPM_M_MAX 64
 #define PHIPM_P_MAX 8

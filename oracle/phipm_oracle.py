@@ -54,6 +54,10 @@ Readings where the paper is silent, garbled or contradicts itself
       tolerance still missed, say), tau changes instead.  Sec. 3.4 does not
       say what happens at the bound; taken literally the rejected attempt
       would repeat unchanged for ever.
+  R20 phip, the fixed-dimension variant of Sec. 4.2 (the same code with m
+      held constant), is this algorithm with the m branch never taken: m
+      stays m_init (a happy breakdown shortens it as in R12) and every
+      attempt updates tau.
 """
 from __future__ import annotations
 
@@ -72,6 +76,7 @@ DEFAULTS = dict(
     breakdown_tol=1e-12,
     max_steps=1_000_000,
     max_rejects=1_000_000,
+    adapt_m=True,       # False: the fixed-dimension variant phip of Sec. 4.2
 )
 
 
@@ -442,7 +447,7 @@ def phipm(t_end: float, A, b, tol: float = 1e-7, symm: int = -1, params: dict | 
             c_tau = total_cost(tau_new, m, t_left, p, nnz, n, M, symmetric)
             c_m = total_cost(tau_used, m_new, t_left, p, nnz, n, M, symmetric)
             m_cand = min(max(m_new, (3 * m) // 4, 1), math.ceil(4 * m / 3), m_max)
-            if c_tau < c_m or m_cand == m:              # Algorithm 3 branch; reading R19 at the m bounds
+            if c_tau < c_m or m_cand == m or not prm["adapt_m"]:   # Algorithm 3 branch; R19; phip
                 tau = min(max(tau_new, tau_used / 5.0), 2.0 * tau_used, t_left)
                 branch = "tau"
             else:
@@ -473,6 +478,15 @@ def phipm(t_end: float, A, b, tol: float = 1e-7, symm: int = -1, params: dict | 
         t = t_end if last else t + tau_used
         tau = min(tau, t_end - t) if t < t_end else tau
     return u, stats
+
+
+def phip(t_end: float, A, b, tol: float = 1e-7, symm: int = -1, m: int = 30,
+         params: dict | None = None, trace: list | None = None):
+    """The fixed-dimension variant of Sec. 4.2 (m = 30 there): phipm with adapt_m off (R20).
+    m_max keeps its default (it enters only Eq. tau_0 through m_bar)."""
+    prm = dict(params or {})
+    prm.update(adapt_m=False, m_init=m)
+    return phipm(t_end, A, b, tol, symm, prm, trace)
 
 
 def shifted_inputs(b: list, t1: float) -> list:

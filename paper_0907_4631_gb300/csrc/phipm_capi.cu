@@ -251,7 +251,7 @@ static bool params_ok(const phipm_params& p, std::string& why) {
     why = "unknown precision";
     return false;
   }
-  if (p.controller != 0 && p.controller != 1) { why = "unknown controller"; return false; }
+  if (p.controller < 0 || p.controller > 2) { why = "unknown controller"; return false; }
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
   return true;
 }
@@ -391,6 +391,7 @@ static DevParams make_params(const phipm_params& p) {
   d.breakdown_tol = p.breakdown_tol;
   d.m_init = p.m_init;
   d.m_max = p.m_max;
+  d.fixed_m = (p.controller == PHIPM_CTRL_FIXED_M) ? 1 : 0;
   d.max_steps = p.max_steps;
   d.max_rejects = p.max_rejects;
   d.timeout_cycles = p.timeout_cycles;

@@ -1734,10 +1734,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           const double c_tau = ceil(t_left / tau_new) * C1((double)m);
           const double c_m = ceil(t_left / tau_used) * C1((double)m_new);
           // m within a factor 4/3 of the current one and within [1, m_max]; when that
-          // leaves m as it is (m at a bound), only a change of tau can alter the attempt
+          // leaves m as it is (m at a bound), only a change of tau can alter the attempt.
+          // The fixed-dimension variant (phip) always changes tau.
           const int m_cand = min(min(max(max(m_new, (3 * m) / 4), 1), (4 * m + 2) / 3), m_max);
           bool branch_tau;
-          if (c_tau < c_m || m_cand == m) {
+          if (c_tau < c_m || m_cand == m || prm.fixed_m) {
             c.tau = fmin(fmin(fmax(tau_new, tau_used / 5.0), 2.0 * tau_used), t_left);
             branch_tau = true;
           } else {

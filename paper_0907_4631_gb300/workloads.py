@@ -171,6 +171,29 @@ def stencil_to_csr(st: Stencil) -> CSR:
     return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), vals)
 
 
+def nine_point(N: int, center: float = 8.0, neighbour: float = -1.0) -> CSR:
+    """Nine-point matrix on an N x N grid of unknowns (x fastest): every unknown couples
+    to the up to eight grid neighbours with |dx|, |dy| <= 1.  Its sparsity is that of
+    the nine-point Laplacian of Sec. 4.2 (N = 30: n = 900, nnz = (3N-2)^2 = 7,744).
+    The default values (8 on the diagonal, -1 off it) make a symmetric positive
+    definite matrix with eigenvalues in (0, 12)."""
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    x, y = idx % N, idx // N
+    rows, cols, vals = [], [], []
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            mask = (x + dx >= 0) & (x + dx < N) & (y + dy >= 0) & (y + dy < N)
+            rows.append(idx[mask])
+            cols.append(idx[mask] + dx + N * dy)
+            vals.append(np.full(int(mask.sum()), center if dx == 0 and dy == 0 else neighbour))
+    rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return CSR(n, np.cumsum(rowptr).astype(np.int32), cols[order].astype(np.int32), vals[order].astype(np.float64))
+
+
 def dense_to_csr(A: np.ndarray) -> CSR:
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -294,3 +317,128 @@ def peclet_convdiff_problems(count: int = 1024, N: int = 128, pe_lo: float = 1.0
         probs.append(Problem(f"pe_{i}", stencil_to_csr(st), _normal_vectors(s, st.n, p + 1), t_end, tol, 0,
                              meta=dict(pe=pe, angle=ang, seed=s, stencil=st)))
     return probs
+
+
+def nine_point_phi_sum_problem(N: int = 30, p: int = 4, t_end: float = 2.0,
+                               tol: float = 2.0 ** -26) -> Problem:
+    """Sec. 4.2, Experiment 2 on the nine-point matrix: sum_{k<=4} t^k phi_k(tA) b_k with
+    every b_k = [1, ..., 1], t = 2, Tol = sqrt(machine epsilon).  The paper's matrix values
+    are not printed; the stand-in is A = -S with S = nine_point(N) (diagonal 8, off-diagonal
+    -1), so that e^{tA} decays as the Laplacian's does."""
+    S = nine_point(N)
+    A = CSR(S.n, S.rowptr, S.colind, -S.values)
+    return Problem(f"ninepoint{N}_phi{p}", A, [np.ones(S.n) for _ in range(p + 1)], t_end, tol, 1,
+                   meta=dict(N=N))
+
+
+def nine_point_round_trip(N: int = 30, t_end: float = 2.0, tol: float = 1e-14) -> tuple:
+    """Sec. 4.2, Experiment 1's third case: w = e^{tA} b_0, then e^{-tA} w, which returns b_0
+    in exact arithmetic; b_0 = [1, ..., 1], t = 2, Tol = 1e-14, A = -nine_point(N).
+    Returns (A, -A) as CSR, b_0, t_end and tol."""
+    S = nine_point(N)
+    A = CSR(S.n, S.rowptr, S.colind, -S.values)
+    B = CSR(S.n, S.rowptr, S.colind, S.values.copy())
+    return A, B, np.ones(S.n), t_end, tol
+
+
+@dataclasses.dataclass
+class HestonGrid:
+    """Grid and coefficients of the Heston PDE of Sec. 4.1 (u' = A u + b_1)."""
+    ns: int = 100           # points in s: s_i = i ds, i = 1..ns (s = 0 and s = S are not grid points)
+    nv: int = 51            # points in v: v_j = j dv, j = 0..nv-1 (v = 0 is, v = V is not)
+    K: float = 100.0        # strike
+    S: float = 800.0        # 8 K
+    V: float = 5.0
+    kappa: float = 2.0
+    eta: float = 0.2        # the mean level of v (the parameter list prints it as nu)
+    lam: float = 0.3
+    rho: float = 0.8
+    rd: float = 0.03
+    rf: float = 0.0
+    T: float = 1.0
+
+    @property
+    def ds(self) -> float:
+        return self.S / (self.ns + 1)
+
+    @property
+    def dv(self) -> float:
+        return self.V / self.nv
+
+    def s(self) -> np.ndarray:
+        return self.ds * np.arange(1, self.ns + 1)
+
+    def v(self) -> np.ndarray:
+        return self.dv * np.arange(self.nv)
+
+
+def heston_operator(g: HestonGrid | None = None) -> tuple:
+    """Assemble the semi-discrete Heston system u' = A u + b_1, u(0) = b_0 of Sec. 4.1.
+
+    Unknowns U_{i,j} = U(s_i, v_j) numbered i + ns j (s fastest).  Rows with v_j > 0 use
+    the printed second-order differences for U_s, U_ss, U_v, U_vv and U_sv of
+        U_t = v s^2/2 U_ss + rho lam v s U_sv + lam^2 v/2 U_vv + (rd - rf) s U_s
+              + kappa (eta - v) U_v - rd U;
+    rows with v = 0 use the boundary equation U_t = (rd - rf) s U_s + kappa eta U_v - rd U
+    with the printed one-sided U_v.  Boundary data: U = 0 at s = 0 and U = s at v = V
+    (both into b_1), U_s = 1 at s = S through the ghost value U(S, v) = U(s_ns, v) + ds.
+    b_0 is the payoff max(s - K, 0).  Returns (CSR A, b_0, b_1, grid)."""
+    g = g or HestonGrid()
+    ns, nv, ds, dv = g.ns, g.nv, g.ds, g.dv
+    s, v = g.s(), g.v()
+    n = ns * nv
+    rows, cols, vals = [], [], []
+    b1 = np.zeros(n)
+
+    def add(r, i, j, c):
+        """Coefficient c on U at grid index (i, j); i = -1 is s = 0, i = ns is s = S, j = nv is v = V."""
+        if j == nv:
+            s_i = ds * (i + 1)
+            b1[r] += c * s_i                  # U(s, V) = s
+        elif i < 0:
+            pass                              # U(0, v) = 0
+        elif i == ns:
+            rows.append(r); cols.append(ns - 1 + ns * j); vals.append(c)
+            b1[r] += c * ds                   # ghost: U(S, v) = U(s_ns, v) + ds
+        else:
+            rows.append(r); cols.append(i + ns * j); vals.append(c)
+
+    for j in range(nv):
+        for i in range(ns):
+            r = i + ns * j
+            a_s = (g.rd - g.rf) * s[i] / (2 * ds)
+            if j == 0:
+                c = g.kappa * g.eta / (2 * dv)
+                add(r, i + 1, 0, a_s); add(r, i - 1, 0, -a_s)
+                add(r, i, 0, -3 * c); add(r, i, 1, 4 * c); add(r, i, 2, -c)
+            else:
+                a_ss = 0.5 * v[j] * s[i] ** 2 / ds ** 2
+                a_vv = 0.5 * g.lam ** 2 * v[j] / dv ** 2
+                a_v = g.kappa * (g.eta - v[j]) / (2 * dv)
+                a_sv = g.rho * g.lam * v[j] * s[i] / (4 * ds * dv)
+                add(r, i + 1, j, a_ss + a_s); add(r, i - 1, j, a_ss - a_s); add(r, i, j, -2 * a_ss)
+                add(r, i, j + 1, a_vv + a_v); add(r, i, j - 1, a_vv - a_v); add(r, i, j, -2 * a_vv)
+                add(r, i + 1, j + 1, a_sv); add(r, i - 1, j - 1, a_sv)
+                add(r, i - 1, j + 1, -a_sv); add(r, i + 1, j - 1, -a_sv)
+            add(r, i, j, -g.rd)
+    rows, cols, vals = np.asarray(rows), np.asarray(cols), np.asarray(vals, dtype=np.float64)
+    # merge duplicates (ghost folding), drop exact zeros, sort columns within rows
+    key = rows.astype(np.int64) * n + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    uniq, start = np.unique(key, return_index=True)
+    merged = np.add.reduceat(vals, start)
+    keep = merged != 0.0
+    uniq, merged = uniq[keep], merged[keep]
+    r_u = (uniq // n).astype(np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r_u + 1, 1)
+    A = CSR(n, np.cumsum(rowptr).astype(np.int32), (uniq % n).astype(np.int32), merged)
+    b0 = np.maximum(np.tile(s, nv) - g.K, 0.0)
+    return A, b0, b1, g
+
+
+def heston_problem(tol: float = 1e-4) -> Problem:
+    """Sec. 4.1: u(T) = e^{TA} b_0 + T phi_1(TA) b_1 for the 100 x 51 Heston grid, T = 1."""
+    A, b0, b1, g = heston_operator()
+    return Problem(f"heston_{g.ns}x{g.nv}", A, [b0, b1], g.T, tol, 0, meta=dict(grid=g))

@@ -70,6 +70,10 @@ def test_invalid_params_rejected_without_gpu():
     h = ctypes.c_void_p()
     assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
     assert not h.value
+    p = pm.default_params()
+    p.controller = pm.CTRL_FIXED_M + 1
+    assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
+    assert not h.value
 
 
 def test_tuning_entry_points_reject_null_handles(tmp_path):

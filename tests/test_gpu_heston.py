@@ -1,0 +1,33 @@
+"""The Heston workload of Sec. 4.1 (nonsymmetric, p = 1, inhomogeneous) on the CUDA path.
+Its controller trajectory changes with 1-ulp changes of A (the oracle itself takes 206 or
+242 steps for A and A perturbed by one ulp), so the step counts of the two sides may
+differ; the results agree far inside the bar because both meet Tol = 1e-4 on a solution
+of norm ~2.8e4."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import phipm_oracle as O
+from paper_0907_4631_gb300 import phipm as pm
+from paper_0907_4631_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,team", [("f64", 1), ("f64pair", 1), ("f64pair", 4), ("f64", 0)])
+def test_heston_matches_oracle(prec, team):
+    pr = wl.heston_problem()
+    s = pm.Phipm(prec)
+    if team:
+        s.set_team(team)
+    b = [torch.as_tensor(x).cuda() for x in pr.b]
+    u, st, _ = s.solve(pr.t_end, pm.DeviceOperator(pr.op), b, pr.tol, 0)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    assert np.linalg.norm(u - ref) <= 1e-8 * np.linalg.norm(ref)
+    fine, _ = O.phipm(pr.t_end, pr.op, pr.b, 1e-9, 0)
+    assert np.linalg.norm(u - fine) <= pr.tol
+    assert st["err_est_sum"] <= 1.2 * pr.tol
+    assert 0.5 * rst.steps <= st["steps"] <= 2 * rst.steps
