@@ -47,10 +47,10 @@ struct PmShared {
   float ucf[PM_NSLOT];
   df32 ucd[PM_NSLOT];
   double dred[PM_DRED];                // per-segment partial dots of one pass
-  double wy[PM_WARPS][PM_NA];          // per-warp column of the exponential's solve
   double lu[PM_NA2];                   // LU factors of the Pade denominator (every CTA its own)
   double rdiag[PM_NA];                 // reciprocals of U's diagonal
   int piv[PM_NA];
+  int perm[PM_NA];                     // the row interchanges of the LU as one permutation
   float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
 };
@@ -1007,15 +1007,18 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     __syncthreads();
     for (int k = 0; k < N; ++k) {
       if (warp == 0) {
-        double best = -1.0;
+        // pivot search on integer keys: the bit patterns of |x| order as the values do,
+        // and integer compares stay off the FP64 pipe (on GB300 every FP64 warp
+        // instruction, compares included, occupies it for about 64 cycles)
+        long long best = -1;
         int bi = k;
         for (int i = k + lane; i < N; i += 32) {
-          const double a = fabs(L[i * PM_NA + k]);
+          const long long a = __double_as_longlong(L[i * PM_NA + k]) & 0x7fffffffffffffffll;
           if (a > best) { best = a; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
@@ -1034,44 +1037,53 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
         }
       }
       __syncthreads();
-      for (int i = k + 1 + warp; i < N; i += PM_WARPS) {
-        const double lik = L[i * PM_NA + k];
-        for (int j = k + 1 + lane; j < N; j += 32) L[i * PM_NA + j] = fma(-lik, L[k * PM_NA + j], L[i * PM_NA + j]);
+      // trailing update, its r x r elements spread flat over the CTA (fewest FP64 warp
+      // instructions: their cost does not depend on how many lanes are active)
+      const int r = N - k - 1;
+      for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int i = k + 1 + e / r, j = k + 1 + e % r;
+        L[i * PM_NA + j] = fma(-L[i * PM_NA + k], L[k * PM_NA + j], L[i * PM_NA + j]);
       }
       __syncthreads();
     }
+    if (threadIdx.x == 0) {            // the row interchanges as one permutation: row i of P R = row perm[i] of P
+      for (int i = 0; i < N; ++i) s.perm[i] = i;
+      for (int k = 0; k < N; ++k) {
+        const int pk = s.piv[k];
+        if (pk != k) { const int t = s.perm[k]; s.perm[k] = s.perm[pk]; s.perm[pk] = t; }
+      }
+    }
+    __syncthreads();
   }
-  // R = Q^{-1} P, one warp per column, columns split over the team
+  // R = Q^{-1} P on the CTA's columns [c0, c1) (columns split over the team), in place in
+  // R: every substitution step updates all of the CTA's columns at once, the elements
+  // spread flat over its threads (one CTA-wide barrier per step)
   {
     int c0, c1;
     split_range(N, rk, G, c0, c1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nc = c1 - c0;
     const double* L = s.lu;
-    double* yv = s.wy[warp];
-    for (int j = c0 + warp; j < c1; j += PM_WARPS) {
-      for (int i = lane; i < N; i += 32) yv[i] = ldx<Team::multi>(&Pm[i * PM_NA + j]);
-      __syncwarp();
-      if (lane == 0)
-        for (int k = 0; k < N; ++k) {
-          const int pk = s.piv[k];
-          if (pk != k) { const double t = yv[k]; yv[k] = yv[pk]; yv[pk] = t; }
-        }
-      __syncwarp();
-      // column-oriented substitutions: each step is one FMA per lane, no reduction
-      for (int k = 0; k + 1 < N; ++k) {      // unit lower triangular
-        const double yk = yv[k];
-        for (int i = k + 1 + lane; i < N; i += 32) yv[i] = fma(-L[i * PM_NA + k], yk, yv[i]);
-        __syncwarp();
+    for (int e = threadIdx.x; e < N * nc; e += blockDim.x) {
+      const int i = e / nc, j = c0 + e % nc;
+      R[i * PM_NA + j] = ldx<Team::multi>(&Pm[s.perm[i] * PM_NA + j]);
+    }
+    __syncthreads();
+    for (int k = 0; k + 1 < N && nc > 0; ++k) {     // unit lower triangular
+      const int r = N - k - 1;
+      for (int e = threadIdx.x; e < r * nc; e += blockDim.x) {
+        const int i = k + 1 + e / nc, j = c0 + e % nc;
+        R[i * PM_NA + j] = fma(-L[i * PM_NA + k], R[k * PM_NA + j], R[i * PM_NA + j]);
       }
-      for (int k = N - 1; k >= 0; --k) {     // upper triangular
-        const double yk = yv[k] * s.rdiag[k];
-        __syncwarp();
-        if (lane == 0) yv[k] = yk;
-        for (int i = lane; i < k; i += 32) yv[i] = fma(-L[i * PM_NA + k], yk, yv[i]);
-        __syncwarp();
+      __syncthreads();
+    }
+    for (int k = N - 1; k >= 0 && nc > 0; --k) {    // upper triangular
+      for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) R[k * PM_NA + j] *= s.rdiag[k];
+      __syncthreads();
+      for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+        const int i = e / nc, j = c0 + e % nc;
+        R[i * PM_NA + j] = fma(-L[i * PM_NA + k], R[k * PM_NA + j], R[i * PM_NA + j]);
       }
-      for (int i = lane; i < N; i += 32) R[i * PM_NA + j] = yv[i];
-      __syncwarp();
+      __syncthreads();
     }
   }
   if (!team.sync()) return false;
@@ -1723,7 +1735,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           if (isfinite(m_new_real)) m_new = (int)fmin(fmax(ceil(m_new_real), 1.0), (double)m_max);
           else m_new = (m_new_real < 0.0) ? 1 : m_max;
           // cost model, Eqs. (4), (5), (8) with R13-R15
-          const double Mf = 44.0 / 3.0 + 2.0 * pm_squarings(c.norm1, prm.theta13);
+          const double Mf = 44.0 / 3.0 + 2.0 * c.sq;     // c.sq = the squarings of this attempt's exponential
           const double t_left = c.t_end - c.t;
           const double nnzA = (double)P.A.nnz;
           auto C1 = [&](double mm) {

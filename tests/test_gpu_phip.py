@@ -59,18 +59,22 @@ def test_phip_convdiff_matches_oracle(prec, team):
     assert st["steps"] == rst.steps and st["rejects"] == rst.rejects
 
 
+@pytest.mark.parametrize("prec", ["f64", "f64pair"])
 @pytest.mark.parametrize("ctrl", [pm.CTRL_PAPER, pm.CTRL_FIXED_M])
-def test_nine_point_round_trip(ctrl):
+def test_nine_point_round_trip(prec, ctrl):
     """e^{-tA} e^{tA} b_0 = b_0 (t = 2, Tol = 1e-14): the forward result matches the oracle,
-    and the round trip returns b_0 to the accuracy the reverse amplification allows."""
+    and the round trip returns b_0 to the accuracy the reverse amplification allows: the
+    reverse pass multiplies the forward pass's rounding error in the top eigenmode by up to
+    e^{2 * 12}, about 2e-6 relative per unit roundoff of 2^-53 (IEEE FP64 basis) and 32 times
+    that with the 48-bit float-pair basis."""
     A, B, b0, t, tol = wl.nine_point_round_trip()
-    s = pm.Phipm("f64pair", controller=ctrl, m_init=30 if ctrl == pm.CTRL_FIXED_M else 10)
+    s = pm.Phipm(prec, controller=ctrl, m_init=30 if ctrl == pm.CTRL_FIXED_M else 10)
     prm = dict(adapt_m=False, m_init=30) if ctrl == pm.CTRL_FIXED_M else None
     w, _ = _solve(s, A, [b0], t, tol, 1)
     w_ref, _ = O.phipm(t, A, [b0], tol, 1, params=prm)
     assert _rel(w, w_ref) <= TOL64
     r, _ = _solve(s, B, [w], t, tol, 1)
-    assert _rel(r, b0) <= 1e-5
+    assert _rel(r, b0) <= (1e-5 if prec == "f64" else 3e-4)
 
 
 @pytest.mark.parametrize("ctrl", [pm.CTRL_PAPER, pm.CTRL_FIXED_M])
