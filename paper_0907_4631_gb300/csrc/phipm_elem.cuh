@@ -58,6 +58,31 @@ __device__ __forceinline__ df32 f2_round(const F2Acc& a) {
   ef_two_sum(a.hi, a.lo, r.hi, r.lo);
   return r;
 }
+// Partial sums are combined across lanes, warps and CTAs as normalised float pairs
+// (for the FP32 and float-pair bases): on GB300 every FP64 warp instruction holds the
+// FP64 pipe for about 64 cycles however few lanes are active, so FP64 shuffle-adds
+// would dominate a reduction tree.  f2_add is Dekker's pair addition (TwoSum of the
+// high parts, the low parts added to the error, renormalised by TwoSum); it is exact
+// up to about 2^-47 of |a| + |b| and commutative bit for bit.
+__device__ __forceinline__ F2Acc f2_norm(const F2Acc& a) {
+  F2Acc r;
+  ef_two_sum(a.hi, a.lo, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ F2Acc f2_add(const F2Acc& a, const F2Acc& b) {
+  float s, e;
+  ef_two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  F2Acc r;
+  ef_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ F2Acc f2_split(double x) {   // x to about 48 bits
+  F2Acc r;
+  r.hi = __double2float_rn(x);
+  r.lo = __double2float_rn(x - (double)r.hi);
+  return r;
+}
 __device__ __forceinline__ df32 df_from_d(double x) {
   df32 r;
   r.hi = __double2float_rn(x);
@@ -90,8 +115,13 @@ template <class S> struct Elem;
 template <> struct Elem<double> {
   static constexpr int kind = 0;
   typedef double Acc;   // dot accumulator
+  typedef double Red;   // partial sum as combined across lanes, warps and CTAs
   typedef double Coef;  // Gram-Schmidt coefficient as used in updates
   __device__ static __forceinline__ Acc zero() { return 0.0; }
+  __device__ static __forceinline__ Red red_of(const Acc& a, const Acc& b) { return a + b; }
+  __device__ static __forceinline__ Red red_add(const Red& a, const Red& b) { return a + b; }
+  __device__ static __forceinline__ Red red_zero() { return 0.0; }
+  __device__ static __forceinline__ double red_val(const Red& a) { return a; }
   __device__ static __forceinline__ void dot(Acc& a, double x, double y) { a = fma(x, y, a); }
   __device__ static __forceinline__ double val(const Acc& a) { return a; }
   __device__ static __forceinline__ double from_d(double x) { return x; }
@@ -104,8 +134,13 @@ template <> struct Elem<double> {
 template <> struct Elem<float> {
   static constexpr int kind = 1;
   typedef F2Acc Acc;
+  typedef F2Acc Red;
   typedef float Coef;
   __device__ static __forceinline__ Acc zero() { return f2_zero(); }
+  __device__ static __forceinline__ Red red_of(const Acc& a, const Acc& b) { return f2_add(f2_norm(a), f2_norm(b)); }
+  __device__ static __forceinline__ Red red_add(const Red& a, const Red& b) { return f2_add(a, b); }
+  __device__ static __forceinline__ Red red_zero() { return f2_zero(); }
+  __device__ static __forceinline__ double red_val(const Red& a) { return f2_value(a); }
   __device__ static __forceinline__ void dot(Acc& a, float x, float y) { f2_add_prod(a, x, y); }
   __device__ static __forceinline__ double val(const Acc& a) { return f2_value(a); }
   __device__ static __forceinline__ float from_d(double x) { return (float)x; }
@@ -118,8 +153,13 @@ template <> struct Elem<float> {
 template <> struct Elem<df32> {
   static constexpr int kind = 2;
   typedef F2Acc Acc;
+  typedef F2Acc Red;
   typedef df32 Coef;
   __device__ static __forceinline__ Acc zero() { return f2_zero(); }
+  __device__ static __forceinline__ Red red_of(const Acc& a, const Acc& b) { return f2_add(f2_norm(a), f2_norm(b)); }
+  __device__ static __forceinline__ Red red_add(const Red& a, const Red& b) { return f2_add(a, b); }
+  __device__ static __forceinline__ Red red_zero() { return f2_zero(); }
+  __device__ static __forceinline__ double red_val(const Red& a) { return f2_value(a); }
   __device__ static __forceinline__ void dot(Acc& a, df32 x, df32 y) { f2_add_prod(a, x, y); }
   __device__ static __forceinline__ double val(const Acc& a) { return f2_value(a); }
   __device__ static __forceinline__ df32 from_d(double x) { return df_from_d(x); }

@@ -62,6 +62,36 @@ struct PmWork {
 
 #define PM_PSTRIDE (2 * PM_NSLOT + 4)
 
+// Sums of E::Red partials across a warp (float pairs for the FP32 and float-pair
+// bases, FP64 otherwise), and their 8-byte slots in shared memory.
+template <class E>
+__device__ __forceinline__ typename E::Red red_warp_sum(typename E::Red v) {
+  if constexpr (E::kind == 0) {
+    return pm_warp_sum(v);
+  } else {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      F2Acc t;
+      t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+      t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+      v = f2_add(v, t);
+    }
+    return v;
+  }
+}
+template <class R>
+__device__ __forceinline__ void red_put(double* p, const R& r) {
+  static_assert(sizeof(R) == sizeof(double), "a partial fills one 8-byte slot");
+  memcpy(p, &r, sizeof(R));
+}
+template <class R>
+__device__ __forceinline__ R red_get(const double* p) {
+  R r;
+  memcpy(&r, p, sizeof(R));
+  return r;
+}
+
+
 // ------------------------------------------------------------------------------------
 // team reductions of K values held in s.coef[0..K) by each CTA
 // ------------------------------------------------------------------------------------
@@ -69,46 +99,103 @@ struct PmWork {
 // s.coef[0..K).  The G x K loads are cut into units (k, block of CTAs) so that each
 // thread has up to PM_RB independent L2 loads in flight (a lane-strided loop leaves
 // one load per lane outstanding and pays the L2 latency G / 32 times per k); units
-// are folded in a fixed order, so every CTA gets bit-identical results.
+// are folded in a fixed order, so every CTA gets bit-identical results.  With PAIR
+// the partials are float pairs (F2Acc in the 8-byte slots) folded by f2_add on the
+// FP32 pipe (the FP32 and float-pair bases; every CTA folds all G x K partials).
 #define PM_RB 16
-template <bool MAX>
-__device__ __forceinline__ void team_fold(PmShared& s, const double* P, int G, int K) {
+template <bool PAIR>
+__device__ __forceinline__ void team_fold_sum(PmShared& s, const double* P, int G, int K) {
   if (K <= 0) { __syncthreads(); return; }
   int nb = (G + PM_RB - 1) / PM_RB;
   nb = max(1, min(nb, PM_DRED / K));
   const int gpb = (G + nb - 1) / nb;          // CTAs per unit
-  const double id = MAX ? -INFINITY : 0.0;
   for (int u = threadIdx.x; u < K * nb; u += blockDim.x) {
     const int k = u / nb, b = u - k * nb;
     const int g0 = b * gpb, g1 = min(G, g0 + gpb);
-    double a = id;
+    if constexpr (PAIR) {
+      F2Acc a = f2_zero();
+      for (int g = g0; g < g1; g += PM_RB) {
+        float2 v[PM_RB];
+#pragma unroll
+        for (int q = 0; q < PM_RB; ++q)
+          v[q] = (g + q < g1) ? __ldcg(reinterpret_cast<const float2*>(&P[(size_t)(g + q) * PM_PSTRIDE + k]))
+                              : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < PM_RB; ++q) {
+          F2Acc t;
+          t.hi = v[q].x;
+          t.lo = v[q].y;
+          a = f2_add(a, t);
+        }
+      }
+      red_put(&s.dred[u], a);
+    } else {
+      double a = 0.0;
+      for (int g = g0; g < g1; g += PM_RB) {
+        double v[PM_RB];
+#pragma unroll
+        for (int q = 0; q < PM_RB; ++q) v[q] = (g + q < g1) ? __ldcg(&P[(size_t)(g + q) * PM_PSTRIDE + k]) : 0.0;
+#pragma unroll
+        for (int q = 0; q < PM_RB; ++q) a = a + v[q];
+      }
+      s.dred[u] = a;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    if constexpr (PAIR) {
+      F2Acc a = red_get<F2Acc>(&s.dred[k * nb]);
+      for (int b = 1; b < nb; ++b) a = f2_add(a, red_get<F2Acc>(&s.dred[k * nb + b]));
+      s.coef[k] = f2_value(a);
+    } else {
+      double a = s.dred[k * nb];
+      for (int b = 1; b < nb; ++b) a = a + s.dred[k * nb + b];
+      s.coef[k] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// the same fold for maxima (FP64; rare: norms of A)
+__device__ __forceinline__ void team_fold_max(PmShared& s, const double* P, int G, int K) {
+  if (K <= 0) { __syncthreads(); return; }
+  int nb = (G + PM_RB - 1) / PM_RB;
+  nb = max(1, min(nb, PM_DRED / K));
+  const int gpb = (G + nb - 1) / nb;
+  for (int u = threadIdx.x; u < K * nb; u += blockDim.x) {
+    const int k = u / nb, b = u - k * nb;
+    const int g0 = b * gpb, g1 = min(G, g0 + gpb);
+    double a = -INFINITY;
     for (int g = g0; g < g1; g += PM_RB) {
       double v[PM_RB];
 #pragma unroll
-      for (int q = 0; q < PM_RB; ++q) v[q] = (g + q < g1) ? __ldcg(&P[(size_t)(g + q) * PM_PSTRIDE + k]) : id;
+      for (int q = 0; q < PM_RB; ++q) v[q] = (g + q < g1) ? __ldcg(&P[(size_t)(g + q) * PM_PSTRIDE + k]) : -INFINITY;
 #pragma unroll
-      for (int q = 0; q < PM_RB; ++q) a = MAX ? fmax(a, v[q]) : a + v[q];
+      for (int q = 0; q < PM_RB; ++q) a = fmax(a, v[q]);
     }
     s.dred[u] = a;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double a = s.dred[k * nb];
-    for (int b = 1; b < nb; ++b) a = MAX ? fmax(a, s.dred[k * nb + b]) : a + s.dred[k * nb + b];
+    for (int b = 1; b < nb; ++b) a = fmax(a, s.dred[k * nb + b]);
     s.coef[k] = a;
   }
   __syncthreads();
 }
 
-template <class Team>
+template <bool PAIR, class Team>
 __device__ bool team_sum(const Team& team, PmShared& s, int K, const PmWork& w, int& parity) {
   if (!Team::multi) { __syncthreads(); return true; }
   const int G = team.size(), r = team.rank();
   double* P = w.partials + (size_t)parity * G * PM_PSTRIDE;
   parity ^= 1;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    if constexpr (PAIR) red_put(&P[(size_t)r * PM_PSTRIDE + k], f2_split(s.coef[k]));
+    else P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
+  }
   if (!team.sync()) return false;
-  team_fold<false>(s, P, G, K);
+  team_fold_sum<PAIR>(s, P, G, K);
   return true;
 }
 
@@ -120,7 +207,7 @@ __device__ bool team_max(const Team& team, PmShared& s, int K, const PmWork& w, 
   parity ^= 1;
   for (int k = threadIdx.x; k < K; k += blockDim.x) P[(size_t)r * PM_PSTRIDE + k] = s.coef[k];
   if (!team.sync()) return false;
-  team_fold<true>(s, P, G, K);
+  team_fold_max(s, P, G, K);
   return true;
 }
 
@@ -395,7 +482,7 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
     }
     constexpr int NG = 2;                      // vectors per group
     for (int i0 = 0; i0 < nvec; i0 += NG) {
-      double d[NG];
+      typename E::Red d[NG];
       Quad<S> vq[NG];
 #pragma unroll
       for (int u = 0; u < NG; ++u) {
@@ -417,22 +504,25 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
 #pragma unroll
           for (int k = 0; k < 4; ++k) E::dot(acc, vq[u].x[k], yq.x[k]);
         }
-        d[u] = pm_warp_sum(E::val(acc));
+        d[u] = red_warp_sum<E>(E::red_of(acc, E::zero()));
       }
       if (lane == 0) {
 #pragma unroll
         for (int u = 0; u < NG; ++u) {
           const int i = i0 + u;
-          if (i < nvec) red[i * PM_WARPS + warp] = (base == lo ? 0.0 : red[i * PM_WARPS + warp]) + d[u];
+          if (i < nvec) {
+            double* slot = &red[i * PM_WARPS + warp];
+            red_put(slot, E::red_add(base == lo ? E::red_zero() : red_get<typename E::Red>(slot), d[u]));
+          }
         }
       }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double t = 0.0;
-    for (int w = 0; w < PM_WARPS; ++w) t += red[i * PM_WARPS + w];
-    s.coef[i] = t;
+    typename E::Red t = E::red_zero();
+    for (int w = 0; w < PM_WARPS; ++w) t = E::red_add(t, red_get<typename E::Red>(&red[i * PM_WARPS + w]));
+    s.coef[i] = E::red_val(t);
   }
   __syncthreads();
 }
@@ -447,7 +537,8 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
 // multiple of 64, so quads start on row offsets that are multiples of 4.
 #define PM_DSEG (PM_DRED / PM_WARPS)   // segments per warp
 template <class S>
-__device__ __forceinline__ double dot_segment(const S* __restrict__ v, const S* __restrict__ y, int a, int b) {
+__device__ __forceinline__ typename Elem<S>::Red dot_segment(const S* __restrict__ v, const S* __restrict__ y, int a,
+                                                            int b) {
   typedef Elem<S> E;
   typedef typename E::Acc Acc;
   const int lane = threadIdx.x & 31;
@@ -477,7 +568,7 @@ __device__ __forceinline__ double dot_segment(const S* __restrict__ v, const S* 
     for (int k = 0; k < 4; ++k) E::dot(acc0, v0.x[k], y0.x[k]);
   }
   if (qb + lane < b) E::dot(acc0, v[qb + lane], y[qb + lane]);      // tail: at most 3 rows
-  return E::val(acc0) + E::val(acc1);
+  return E::red_of(acc0, acc1);
 }
 
 template <class S>
@@ -508,18 +599,18 @@ __device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S*
     for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
       const long long r1 = min(rows, r0 + (fend - f));
       const S* v = (i < nv) ? V + (size_t)i * ld : y;
-      const double d = pm_warp_sum(dot_segment<S>(v, y, lo + (int)r0, lo + (int)r1));
-      if (lane == 0) s.dred[warp * PM_DSEG + seg] = d;
+      const typename E::Red d = red_warp_sum<E>(dot_segment<S>(v, y, lo + (int)r0, lo + (int)r1));
+      if (lane == 0) red_put(&s.dred[warp * PM_DSEG + seg], d);
       f += r1 - r0;
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
     const long long fa = (long long)i * rows, fb = fa + rows - 1;
-    double t = 0.0;
+    typename E::Red t = E::red_zero();
     for (long long w = fa / run; w <= fb / run && w < PM_WARPS; ++w)
-      t += s.dred[w * PM_DSEG + (int)(i - (w * run) / rows)];
-    s.coef[i] = t;
+      t = E::red_add(t, red_get<typename E::Red>(&s.dred[w * PM_DSEG + (int)(i - (w * run) / rows)]));
+    s.coef[i] = E::red_val(t);
   }
   __syncthreads();
 }
@@ -620,7 +711,8 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
 // segment leaves two warp-reduced partials in s.dred (even / odd slots).
 template <class S, bool WIDE>
 __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* __restrict__ z,
-                                             const S* __restrict__ w, int a, int b, double& dz, double& dw) {
+                                             const S* __restrict__ w, int a, int b, typename Elem<S>::Red& dz,
+                                             typename Elem<S>::Red& dw) {
   typedef Elem<S> E;
   typedef typename E::Acc Acc;
   const int lane = threadIdx.x & 31;
@@ -682,13 +774,14 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
     for (int k = 0; k < 4; ++k) { E::dot(z0, v0.x[k], z0q.x[k]); E::dot(w0, v0.x[k], w0q.x[k]); }
   }
   if (qb + lane < b) { E::dot(z0, v[qb + lane], z[qb + lane]); E::dot(w0, v[qb + lane], w[qb + lane]); }
-  dz = E::val(z0) + E::val(z1);
-  dw = E::val(w0) + E::val(w1);
+  dz = E::red_of(z0, z1);
+  dw = E::red_of(w0, w1);
 }
 
 template <class S, bool WIDE>
 __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
+  typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + 1;
@@ -708,13 +801,13 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
     for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
       const long long r1 = min(rows, r0 + (fend - f));
       const S* v = (i < nv) ? V + (size_t)i * ld : z;
-      double dz, dw;
+      typename E::Red dz, dw;
       dot_segment2<S, WIDE>(v, z, w, lo + (int)r0, lo + (int)r1, dz, dw);
-      dz = pm_warp_sum(dz);
-      dw = pm_warp_sum(dw);
+      dz = red_warp_sum<E>(dz);
+      dw = red_warp_sum<E>(dw);
       if (lane == 0) {
-        s.dred[warp * PM_DSEG + 2 * seg] = dz;
-        s.dred[warp * PM_DSEG + 2 * seg + 1] = dw;
+        red_put(&s.dred[warp * PM_DSEG + 2 * seg], dz);
+        red_put(&s.dred[warp * PM_DSEG + 2 * seg + 1], dw);
       }
       f += r1 - r0;
     }
@@ -722,14 +815,14 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
   __syncthreads();
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
     const long long fa = (long long)i * rows, fb = fa + rows - 1;
-    double tz = 0.0, tw = 0.0;
+    typename E::Red tz = E::red_zero(), tw = E::red_zero();
     for (long long w2 = fa / run; w2 <= fb / run && w2 < PM_WARPS; ++w2) {
       const int sl = (int)w2 * PM_DSEG + 2 * (int)(i - (w2 * run) / rows);
-      tz += s.dred[sl];
-      tw += s.dred[sl + 1];
+      tz = E::red_add(tz, red_get<typename E::Red>(&s.dred[sl]));
+      tw = E::red_add(tw, red_get<typename E::Red>(&s.dred[sl + 1]));
     }
-    s.coef[i] = tz;
-    s.coef[nvec + i] = tw;
+    s.coef[i] = E::red_val(tz);
+    s.coef[nvec + i] = E::red_val(tw);
   }
   __syncthreads();
 }
@@ -1204,7 +1297,12 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   __syncthreads();
 
 #define PM_SYNC_OR_FAIL() do { if (!team.sync()) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
-#define PM_SUM_OR_FAIL(K) do { if (!team_sum(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
+// team sums: PM_SUM_OR_FAIL in FP64 (norms of the FP64 vectors u and w_p, whose squares
+// can leave the float range); PM_BSUM_OR_FAIL for dot products of basis-type vectors,
+// folded as float pairs when the basis is FP32 or float pairs (their partials were
+// already accumulated in that format)
+#define PM_SUM_OR_FAIL(K) do { if (!team_sum<false>(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
+#define PM_BSUM_OR_FAIL(K) do { if (!team_sum<(Elem<S>::kind != 0)>(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 #define PM_MAX_OR_FAIL(K) do { if (!team_max(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 
   // ---------------- setup (a1): ||A||_inf, ||b_0||_inf, max_k ||b_k||_inf, symmetry; u = b_0
@@ -1427,7 +1525,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             gs_vectors += j;
             __syncthreads();
             dots2_cta<S, !Team::multi>(V, ld, j, zp, Wv, lo, hi, s);
-            PM_SUM_OR_FAIL(2 * (j + 1));
+            PM_BSUM_OR_FAIL(2 * (j + 1));
             // scalars by one warp (||a||^2, a.b); a and b copied by every thread
             if (tid < 32) {
               double aa = 0.0, ab = 0.0;
@@ -1460,7 +1558,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               update_rows2_cold<S>(V, ld, j, ca, E::coef(1.0), zp, Wv, V + (size_t)j * ld, lo, hi);
               __syncthreads();
               dots_cta<S>(V, ld, j, V + (size_t)j * ld, lo, hi, true, s);
-              PM_SUM_OR_FAIL(j + 1);
+              PM_BSUM_OR_FAIL(j + 1);
               if (tid < 32) {
                 double aa = 0.0;
                 for (int k = tid; k < j; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
@@ -1530,7 +1628,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             const int nq = target;
             gs_vectors += nq;
             dots_cta<S>(V, ld, nq, Z, lo, hi, true, s);
-            PM_SUM_OR_FAIL(nq + 1);
+            PM_BSUM_OR_FAIL(nq + 1);
             for (int k = tid; k < nq; k += nth) s.h1[k] = s.coef[k];
             if (tid < 32) {
               double aa = 0.0;
@@ -1549,7 +1647,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               update_rows2_cold<S>(V, ld, nq, ca, E::coef(1.0), Z, Wv, V + (size_t)nq * ld, lo, hi);
               __syncthreads();
               dots_cta<S>(V, ld, nq, V + (size_t)nq * ld, lo, hi, true, s);
-              PM_SUM_OR_FAIL(nq + 1);
+              PM_BSUM_OR_FAIL(nq + 1);
               if (tid < 32) {
                 double aa = 0.0;
                 for (int k = tid; k < nq; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
@@ -1611,7 +1709,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             {
               // Algorithm 2: t_jj = v_j^T y ; y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
               dots_cta<S>(V + (size_t)j * ld, ld, 1, ycur, lo, hi, false, s);
-              PM_SUM_OR_FAIL(1);
+              PM_BSUM_OR_FAIL(1);
               if (tid == 0) {
                 const double tjj = s.coef[0];
                 s.H[j * PM_MAXM + j] = tjj;
@@ -1623,7 +1721,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               else update_rows<S>(ycur, V, ld, 1, hc, lo, hi);
               __syncthreads();
               dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
-              PM_SUM_OR_FAIL(1);
+              PM_BSUM_OR_FAIL(1);
               if (tid == 0) {
                 const double hn = sqrt(s.coef[0]);
                 s.H[(j + 1) * PM_MAXM + j] = hn;
@@ -1916,5 +2014,6 @@ done:
   }
 #undef PM_SYNC_OR_FAIL
 #undef PM_SUM_OR_FAIL
+#undef PM_BSUM_OR_FAIL
 #undef PM_MAX_OR_FAIL
 }

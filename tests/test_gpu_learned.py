@@ -91,7 +91,10 @@ def test_traces_agree_with_stats(solver):
 def test_learned_controller_on_held_out_problems(solver):
     """Train on traces of configuration-1..3 variants, then solve held-out Peclet problems:
     the error estimate still judges every attempt, so accuracy stays at tolerance; the
-    learned first proposal cuts the attempts and the batch's solve time."""
+    learned first proposal cuts the rejected attempts (877 -> 152 in the last measured run),
+    the attempts overall (1390 -> 732) and the batch's solve time.  The trajectories, and so
+    the training set, move with rounding-level changes of the kernels, so the bounds keep
+    a margin below the measured effect."""
     probs = L.training_problems(count=768, seed0=7000)
     recs = L.collect_traces(solver, probs)
     X, T = L.examples_from_traces(recs)
@@ -126,5 +129,8 @@ def test_learned_controller_on_held_out_problems(solver):
           f"{sum(s['rejects'] for s in st1)}; steps {sum(s['steps'] for s in st0)} -> "
           f"{sum(s['steps'] for s in st1)}; Gram-Schmidt vectors {sum(s['gs_vectors'] for s in st0)} -> "
           f"{sum(s['gs_vectors'] for s in st1)}; batch ms {ms0:.2f} -> {ms1:.2f}")
+    rej0 = sum(s["rejects"] for s in st0)
+    rej1 = sum(s["rejects"] for s in st1)
+    assert rej1 < 0.5 * rej0
     assert att1 < 0.6 * att0
     assert ms1 < ms0
