@@ -12,6 +12,7 @@
 // FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
 #define PM_DRED (PM_WARPS * (PM_NSLOT + 2))   // partials of a dot pass (vector x warp) or of a team fold
+#define PM_ZW_BYTES 65536                      // shared staging of the two vectors every product of a dot pass reads
 
 // Scalar state of one problem.  Thread 0 writes it, every thread reads it after
 // the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
@@ -53,6 +54,7 @@ struct PmShared {
   int perm[PM_NA];                     // the row interchanges of the LU as one permutation
   float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
+  alignas(16) unsigned char zw[PM_ZW_BYTES];   // this CTA's rows of z and A z during a dot pass
 };
 
 struct PmWork {
@@ -791,6 +793,31 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
     __syncthreads();
     return;
   }
+  // Every product of the pass reads this CTA's rows of z and w: when they fit, they are
+  // staged in shared memory once, so that L2 serves only the basis vectors (otherwise
+  // z and w would cross L2 once per vector).  Same arithmetic and order either way.
+  // Both staged copies start on 16-byte boundaries (the passes read them with 16-byte
+  // loads at offsets that are multiples of 16 bytes from lo, as they read z and w).
+  constexpr int VEC = 16 / sizeof(S);            // elements per 16-byte copy
+  const long long rows16 = (rows + VEC - 1) / VEC * VEC;
+  const S* zb = z;
+  const S* wb = w;
+  if (2 * rows16 * (long long)sizeof(S) <= (long long)PM_ZW_BYTES) {
+    S* sz = reinterpret_cast<S*>(s.zw);
+    S* sw = sz + rows16;
+    const int nq = (int)(rows / VEC);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      reinterpret_cast<float4*>(sz)[q] = *reinterpret_cast<const float4*>(z + lo + q * VEC);
+      reinterpret_cast<float4*>(sw)[q] = *reinterpret_cast<const float4*>(w + lo + q * VEC);
+    }
+    for (int r = nq * VEC + threadIdx.x; r < rows; r += blockDim.x) {
+      sz[r] = z[lo + r];
+      sw[r] = w[lo + r];
+    }
+    __syncthreads();
+    zb = sz - lo;                                 // indexed by absolute row, like z and w
+    wb = sw - lo;
+  }
   // as in dots_cta: a run meets fewer than 12 vectors, so 2 x 12 slots fit PM_DSEG
   const long long run = (((total + PM_WARPS - 1) / PM_WARPS) + 3) & ~3ll;
   long long f = (long long)warp * run;
@@ -800,9 +827,9 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
     long long r0 = f - (long long)i * rows;
     for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
       const long long r1 = min(rows, r0 + (fend - f));
-      const S* v = (i < nv) ? V + (size_t)i * ld : z;
+      const S* v = (i < nv) ? V + (size_t)i * ld : zb;
       typename E::Red dz, dw;
-      dot_segment2<S, WIDE>(v, z, w, lo + (int)r0, lo + (int)r1, dz, dw);
+      dot_segment2<S, WIDE>(v, zb, wb, lo + (int)r0, lo + (int)r1, dz, dw);
       dz = red_warp_sum<E>(dz);
       dw = red_warp_sum<E>(dw);
       if (lane == 0) {
