@@ -426,7 +426,9 @@ __device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, con
   }
 }
 
-// out[r] = (A x)[r] * sc over this CTA's rows (CSR rows two at a time per thread)
+// out[r] = (A x)[r] * sc over this CTA's rows (CSR rows two at a time per thread,
+// stencil rows two at a time too: their neighbour loads are independent, so a pass has
+// both rows' loads in flight instead of paying the load latency once per row)
 template <class S, class XL>
 __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __restrict__ out,
                                           typename Elem<S>::Coef sc, bool scale, int lo, int hi) {
@@ -441,9 +443,12 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
       if (r2 >= 0) out[r2] = scale ? E::scale(y1, sc) : y1;
     }
   } else {
-    for (int r = lo + threadIdx.x; r < hi; r += nth) {
-      const S y = spmv_row<S>(A, r, x);
-      out[r] = scale ? E::scale(y, sc) : y;
+    for (int r = lo + threadIdx.x; r < hi; r += 2 * nth) {
+      const int r2 = r + nth;
+      const S y0 = spmv_row<S>(A, r, x);
+      const S y1 = (r2 < hi) ? spmv_row<S>(A, r2, x) : y0;
+      out[r] = scale ? E::scale(y0, sc) : y0;
+      if (r2 < hi) out[r2] = scale ? E::scale(y1, sc) : y1;
     }
   }
 }
