@@ -31,3 +31,22 @@ def test_heston_matches_oracle(prec, team):
     assert np.linalg.norm(u - fine) <= pr.tol
     assert st["err_est_sum"] <= 1.2 * pr.tol
     assert 0.5 * rst.steps <= st["steps"] <= 2 * rst.steps
+
+
+@pytest.mark.parametrize("prec,team", [("f64", 1), ("f64pair", 1), ("f64pair", 2)])
+def test_heston_small_grid_vs_dense_truth(prec, team):
+    """20 x 11 grid: the CUDA result against the oracle (<= 1e-8 relative) and against the
+    dense augmented exponential (within Tol)."""
+    from oracle import truth as T
+    A, b0, b1, g = wl.heston_operator(wl.HestonGrid(ns=20, nv=11))
+    tol = 1e-6
+    s = pm.Phipm(prec)
+    s.set_team(team)
+    b = [torch.as_tensor(x).cuda() for x in (b0, b1)]
+    u, st, _ = s.solve(1.0, pm.DeviceOperator(A), b, tol, 0)
+    torch.cuda.synchronize()
+    u = u.cpu().numpy()
+    ref, _ = O.phipm(1.0, A, [b0, b1], tol, 0)
+    assert np.linalg.norm(u - ref) <= 1e-8 * np.linalg.norm(ref)
+    ut = T.solution_dense_augmented(wl.csr_to_dense(A), [b0, b1], 1.0)
+    assert np.linalg.norm(u - ut) <= tol

@@ -82,3 +82,15 @@ def test_heston_oracle_vs_figures_2_3():
     assert st.err_est_sum <= 1.2 * pr.tol
     u_fine, _ = O.phipm(gold["t_end"], pr.op, pr.b, 1e-9, 0)
     assert np.linalg.norm(u - u_fine) <= pr.tol
+
+
+def test_heston_small_grid_vs_dense_augmented():
+    """A 20 x 11 Heston grid (n = 220, the same assembly): the oracle's u(1) against the dense
+    augmented exponential of Sidje's Theorem 1 (scipy's expm), within Tol (absolute, R6)."""
+    A, b0, b1, g = wl.heston_operator(wl.HestonGrid(ns=20, nv=11))
+    tol = 1e-6
+    u, st = O.phipm(1.0, A, [b0, b1], tol, 0)
+    from oracle import truth as T
+    ut = T.solution_dense_augmented(wl.csr_to_dense(A), [b0, b1], 1.0)
+    assert st.steps >= 5
+    assert np.linalg.norm(u - ut) <= tol
