@@ -158,3 +158,27 @@ def test_q_hat_printed_inverted(monkeypatch):
     monkeypatch.setattr(O, "controller", bad)
     with pytest.raises(AssertionError):
         PP.test_controller_hand_cases()
+
+
+def test_phip_that_still_adapts_m(monkeypatch):
+    """phip (R20) with the m branch left on is phipm started at m: the fixed-m pin fails."""
+    import tests.test_oracle_phip as PH
+    monkeypatch.setattr(O, "phip", lambda t_end, A, b, tol=1e-7, symm=-1, m=30, params=None, trace=None:
+                        O.phipm(t_end, A, b, tol, symm, dict(params or {}, m_init=m), trace))
+    with pytest.raises(AssertionError):
+        PH.test_phip_keeps_m_and_meets_tol(6)
+
+
+def test_w_recurrence_without_the_inhomogeneous_terms(monkeypatch):
+    """Eq. (wrecurrence) with the b_{j+l} sums dropped solves u' = Au instead of
+    u' = Au + b_1: the Heston pin against the dense augmented exponential fails."""
+    import tests.test_oracle_heston as HE
+
+    def bad(matvec, u, b, t):
+        W = [u]
+        for j in range(1, len(b)):
+            W.append(matvec(W[j - 1]))
+        return W
+    monkeypatch.setattr(O, "w_recurrence", bad)
+    with pytest.raises(AssertionError):
+        HE.test_heston_small_grid_vs_dense_augmented()
