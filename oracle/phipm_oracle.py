@@ -58,6 +58,10 @@ Readings where the paper is silent, garbled or contradicts itself
       held constant), is this algorithm with the m branch never taken: m
       stays m_init (a happy breakdown shortens it as in R12) and every
       attempt updates tau.
+  R23 phi_method "eigen" (symmetric A): phi_p(tau T) e_1 and phi_{p+1}(tau T) e_1 are
+      taken from the eigen-decomposition of the Lanczos matrix, the direct route
+      Sec. 5 suggests; the cost model still charges the exponential of Eq. (8), so
+      the controller's decisions are those of the augmented route.
 """
 from __future__ import annotations
 
@@ -77,6 +81,7 @@ DEFAULTS = dict(
     max_steps=1_000_000,
     max_rejects=1_000_000,
     adapt_m=True,       # False: the fixed-dimension variant phip of Sec. 4.2
+    phi_method="augmented",   # "eigen": phi of the Lanczos matrix directly (symmetric A only)
 )
 
 
@@ -240,6 +245,45 @@ def expm_pade13(A: np.ndarray, theta13: float = DEFAULTS["theta13"]) -> np.ndarr
     return R
 
 
+# --------------------------------------------------------------------------------------
+# phi of the symmetric Lanczos matrix directly (the alternative Sec. 5 proposes to the
+# augmented exponential when A is symmetric): phi_j(tau T) e_1 = Q phi_j(tau L) Q^T e_1
+# with T = Q L Q^T (numpy's symmetric eigensolver as the library step)
+# --------------------------------------------------------------------------------------
+def phi_scalars(z: np.ndarray, kmax: int) -> np.ndarray:
+    """phi_0(z) .. phi_kmax(z) for real z (rows k).  |z| < 1: the series
+    phi_k(z) = sum_i z^i / (i+k)! of Eq. (phifunctions), summed to 30 terms; otherwise
+    phi_0 = e^z and the recurrence of Eq. (phirelation), phi_k = (phi_{k-1} - 1/(k-1)!)/z."""
+    z = np.asarray(z, dtype=np.float64)
+    out = np.zeros((kmax + 1, z.size))
+    small = np.abs(z) < 1.0
+    for k in range(kmax + 1):
+        zs = z[small]
+        acc = np.zeros_like(zs)
+        term = np.full_like(zs, 1.0 / math.factorial(k))
+        for i in range(30):
+            acc = acc + term
+            term = term * zs / (i + 1 + k)
+        out[k, small] = acc
+    zb = z[~small]
+    prev = np.exp(zb)
+    out[0, ~small] = prev
+    for k in range(1, kmax + 1):
+        prev = (prev - 1.0 / math.factorial(k - 1)) / zb
+        out[k, ~small] = prev
+    return out
+
+
+def phi_columns_tridiagonal(T_m: np.ndarray, tau: float, p: int):
+    """phi_p(tau T_m) e_1 and phi_{p+1}(tau T_m) e_1 (phi_0 = exp for p = 0) of a symmetric
+    tridiagonal T_m, through its eigen-decomposition; the same vectors as the top m
+    entries of columns m+p-1 and m+p of exp(H_hat) (reading R2)."""
+    lam, Q = np.linalg.eigh(T_m)
+    ph = phi_scalars(tau * lam, p + 1)
+    q1 = Q[0, :]
+    return Q @ (ph[p] * q1), Q @ (ph[p + 1] * q1)
+
+
 def expm_cost_factor(norm1: float, theta13: float = DEFAULTS["theta13"]) -> float:
     """M of Eq. (8): 44/3 + 2 ceil(log2(||A||_1/5.37))_+."""
     return 44.0 / 3.0 + 2.0 * squarings(norm1, theta13)
@@ -341,7 +385,7 @@ def omega_ratio(eps: float, tau: float, t_end: float, tol: float) -> float:
 
 
 def krylov_attempt(matvec, krylov, v: np.ndarray, tau: float, m: int, p: int, bd_abs: float,
-                   theta13: float = DEFAULTS["theta13"]):
+                   theta13: float = DEFAULTS["theta13"], phi_method: str = "augmented"):
     """One attempt of Algorithm 3: F ~ tau^p phi_p(tau A) v and its estimate eps.
 
     Krylov projection (Algorithm 1 or 2), augmented matrix (Eq. hathm, R2),
@@ -353,10 +397,13 @@ def krylov_attempt(matvec, krylov, v: np.ndarray, tau: float, m: int, p: int, bd
         return np.zeros(n), 0.0, m, float(p > 0), 0.0
     V, H, m_eff = krylov(matvec, v, m, bd_abs)
     Hh = augmented_matrix(H[:m_eff, :m_eff], tau, p)
-    E = expm_pade13(Hh, theta13)
     norm1_Hh = float(np.max(np.abs(Hh).sum(axis=0)))
-    phi_p = E[:m_eff, m_eff + p - 1] if p >= 1 else E[:m_eff, 0]
-    phi_p1 = E[:m_eff, m_eff + p]
+    if phi_method == "eigen":       # symmetric T_m (Lanczos): phi directly, Sec. 5
+        phi_p, phi_p1 = phi_columns_tridiagonal(H[:m_eff, :m_eff], tau, p)
+    else:
+        E = expm_pade13(Hh, theta13)
+        phi_p = E[:m_eff, m_eff + p - 1] if p >= 1 else E[:m_eff, 0]
+        phi_p1 = E[:m_eff, m_eff + p]
     h_last = H[m_eff, m_eff - 1]
     F = (tau ** p) * beta * (V[:m_eff].T @ phi_p + tau * h_last * phi_p1[m_eff - 1] * V[m_eff])
     eps = (tau ** (p + 1)) * beta * abs(h_last) * abs(phi_p1[m_eff - 1])
@@ -424,7 +471,8 @@ def phipm(t_end: float, A, b, tol: float = 1e-7, symm: int = -1, params: dict | 
         while True:
             tau_used, m_used = tau, m
             F, eps, m_eff, norm1_Hh, beta = krylov_attempt(op.matvec, krylov, W[p], tau_used, m_used, p, bd_abs,
-                                                           prm["theta13"])
+                                                           prm["theta13"],
+                                                           prm["phi_method"] if symmetric else "augmented")
             if beta > 0.0:
                 stats.matvecs += m_eff
                 stats.expms += 1
