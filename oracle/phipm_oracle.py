@@ -62,6 +62,10 @@ Readings where the paper is silent, garbled or contradicts itself
       taken from the eigen-decomposition of the Lanczos matrix, the direct route
       Sec. 5 suggests; the cost model still charges the exponential of Eq. (8), so
       the controller's decisions are those of the augmented route.
+  R24 a matrix-free A (Sec. 3.5 accepts a function computing A b) supplies, besides
+      the product, an upper bound of ||A||_inf and the cost N_A of one product, which
+      Eq. (tau_0), the breakdown threshold and Eq. (4) need; symmetry is not detected
+      (nonsymmetric unless symm = 1), as Sec. 3.5 prescribes for implicit A.
 """
 from __future__ import annotations
 
@@ -89,11 +93,18 @@ DEFAULTS = dict(
 # the operator A (the oracle's own matrix-vector product)
 # --------------------------------------------------------------------------------------
 class Operator:
-    """A as CSR (scipy.sparse product) or as a constant-coefficient stencil."""
+    """A as CSR (scipy.sparse product), as a constant-coefficient stencil, or matrix-free
+    (R24): an object with apply(x) -> A x, n, and the two scalars the method needs from A,
+    norm_inf (an upper bound of ||A||_inf, for Eq. tau_0 and the breakdown threshold) and
+    nnz (the cost of one product in the units of Eq. 4's N_A)."""
 
     def __init__(self, op):
         self.src = op
-        if hasattr(op, "rowptr"):
+        if callable(getattr(op, "apply", None)):
+            self.kind = "function"
+            self.n = int(op.n)
+            self.nnz = int(op.nnz)
+        elif hasattr(op, "rowptr"):
             self.kind = "csr"
             self.n = int(op.n)
             self.M = sp.csr_matrix((np.asarray(op.values, dtype=np.float64),
@@ -105,6 +116,8 @@ class Operator:
             self.nnz = int(op.nnz())
 
     def matvec(self, x: np.ndarray) -> np.ndarray:
+        if self.kind == "function":
+            return np.asarray(self.src.apply(x), dtype=np.float64)
         if self.kind == "csr":
             return self.M @ x
         st = self.src
@@ -122,7 +135,9 @@ class Operator:
         return Y.reshape(-1)
 
     def norm_inf(self) -> float:
-        """||A||_inf, the maximum absolute row sum."""
+        """||A||_inf, the maximum absolute row sum (matrix-free: the bound supplied)."""
+        if self.kind == "function":
+            return float(self.src.norm_inf)
         if self.kind == "csr":
             return float(np.max(np.asarray(abs(self.M).sum(axis=1)).ravel())) if self.n else 0.0
         st = self.src
@@ -132,6 +147,8 @@ class Operator:
         return float(s)
 
     def is_symmetric(self) -> bool:
+        if self.kind == "function":     # not detectable: nonsymmetric unless symm says so (Sec. 3.5)
+            return False
         if self.kind == "csr":
             D = self.M - self.M.T
             return D.count_nonzero() == 0 or float(abs(D).max()) == 0.0

@@ -59,3 +59,4 @@ def test_planted_transposed_eigenvectors(monkeypatch):
     monkeypatch.setattr(O, "phi_columns_tridiagonal", bad)
     with pytest.raises(AssertionError):
         test_tridiagonal_route_equals_augmented_exponential(12, 3, 4.0)
+
