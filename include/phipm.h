@@ -59,6 +59,10 @@ typedef enum {
                              FP64.  Results differ from PHIPM_F64 by about 2^-48 times the
                              cancellation factor ||F|| / ||u|| of Eq. (step).                 */
 } phipm_precision;
+/* Range of the two float-based modes: their Krylov vectors and the partial sums of their
+ * dot products are float pairs or floats, so the candidate vectors, A times them and
+ * their products must stay inside the float range (about 3e38); in practice ||A|| up
+ * to about 1e12.  The norms of u and w_p are always summed in FP64. */
 
 typedef enum { PHIPM_OP_CSR = 0, PHIPM_OP_STENCIL = 1 } phipm_op_kind;
 
