@@ -1,4 +1,9 @@
-"""Build libphipm.so (the C ABI of include/phipm.h) in-tree with nvcc for sm_103a."""
+"""Build libphipm.so (the C ABI of include/phipm.h) in-tree with nvcc for sm_103a.
+
+The nine solver-kernel instances (basis element type x team form) are compiled from
+phipm_kernels.cu as separate objects, in parallel with the C ABI's object, and
+linked into one shared library (no relocatable device code: every kernel is
+launched from the object that defines it)."""
 from __future__ import annotations
 
 import os
@@ -10,8 +15,12 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libphipm.so")
-SOURCES = ["phipm_capi.cu"]
-HEADERS = ["phipm_common.cuh", "phipm_elem.cuh", "phipm_engine.cuh", "phipm_mlp.cuh"]
+SOURCES = ["phipm_capi.cu", "phipm_kernels.cu"]
+HEADERS = ["phipm_common.cuh", "phipm_elem.cuh", "phipm_engine.cuh", "phipm_mlp.cuh", "phipm_mlp_train.cuh",
+           "phipm_launch.h"]
+# (object name, source, macros): the C ABI plus one object per (element type, team form)
+UNITS = [("capi", "phipm_capi.cu", [])] + [
+    (f"kern_e{e}_f{f}", "phipm_kernels.cu", [f"-DPM_ELEM={e}", f"-DPM_FORM={f}"]) for e in range(3) for f in range(3)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -71,15 +80,37 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the library if it is missing or older than its sources; return its path."""
     if not force and not _stale():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + [os.path.join(CSRC, f) for f in SOURCES]
+    objdir = os.path.join(LIBDIR, f"obj{os.getpid()}")
+    os.makedirs(objdir, exist_ok=True)
+    common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+        common.append("-Xptxas=-v")
+
+    def compile_unit(unit):
+        name, src, macros = unit
+        obj = os.path.join(objdir, name + ".o")
+        cmd = common + macros + ["-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return obj, r
+
+    workers = max(1, min(len(UNITS), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(compile_unit, UNITS))
+    for obj, r in results:
+        if r.stdout or r.stderr:
+            sys.stderr.write(r.stdout + r.stderr)
+        if r.returncode != 0:
+            raise subprocess.CalledProcessError(r.returncode, r.args)
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp] + [o for o, _ in results], check=True)
     os.replace(tmp, LIB)
+    for o, _ in results:
+        os.unlink(o)
+    os.rmdir(objdir)
     return LIB
 
 

@@ -1,9 +1,13 @@
-// Host side of the C ABI declared in include/phipm.h, and the kernels that
-// run the device engine (phipm_engine.cuh):
+// Host side of the C ABI declared in include/phipm.h.  The solver kernels that
+// run the device engine (phipm_engine.cuh) live in phipm_kernels.cu and are
+// reached through phipm_launch.h:
 //   k_solve_grid     one problem, every CTA of a cooperative launch;
 //   k_solve_queue    a persistent CTA per slot that pulls problems from an
 //                    atomic queue, largest first (batched form and small
-//                    single problems).
+//                    single problems);
+//   k_solve_cluster  the same queue served by thread-block clusters of K CTAs.
+// This file holds the small kernels (value conversion, the controller network's
+// training) and the allocation-free solve.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -14,126 +18,12 @@
 #include <vector>
 
 #include "phipm.h"
-#include "phipm_engine.cuh"
+#include "phipm_launch.h"
+#include "phipm_mlp_train.cuh"
 
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
-template <class S>
-__global__ void __launch_bounds__(PM_THREADS, 1)
-k_solve_grid(DevProblem P, DevParams prm, DevResult* res, PmWork w, unsigned long long* bar, int* err) {
-  extern __shared__ __align__(16) unsigned char pm_smem[];
-  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
-  GridTeam team{bar, err, prm.timeout_cycles, 0ull};
-  phipm_device<GridTeam, S>(team, P, prm, *res, s, w);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int e = *((volatile int*)err);
-    if (e != 0 && res->status == PM_OK) res->status = e;
-  }
-}
-
-// Workspace of one queue slot (one CTA): V, W, Y and the exponential scratch.
-struct SlotLayout {
-  long long ld;                          // vector stride (elements)
-  long long v_off, w_off, y_off, e_off;  // byte offsets inside the slot
-  long long bytes;                       // bytes per slot (multiple of 256)
-};
-
-template <class S>
-__global__ void __launch_bounds__(PM_THREADS, 1)
-k_solve_queue(const DevProblem* probs, const int* order, int count, DevParams prm, DevResult* res,
-              unsigned char* slots, SlotLayout lay, int* queue) {
-  extern __shared__ __align__(16) unsigned char pm_smem[];
-  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
-  __shared__ int s_next;
-  unsigned char* base = slots + (size_t)blockIdx.x * lay.bytes;
-  CtaTeam team;
-  PmWork w{nullptr, (double*)(base + lay.e_off)};
-  for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
-    __syncthreads();
-    const int q = s_next;
-    __syncthreads();
-    if (q >= count) break;
-    const int id = order[q];
-    DevProblem P = probs[id];
-    P.V = base + lay.v_off;
-    P.W = (double*)(base + lay.w_off);
-    P.Y = base + lay.y_off;
-    P.ld = lay.ld;
-    phipm_device<CtaTeam, S>(team, P, prm, res[id], s, w);
-    __syncthreads();
-  }
-}
-
-// Batched form with a team of K CTAs per problem: each thread-block cluster is one
-// team (rows split over its CTAs, reductions through per-cluster partials, barriers
-// on a counter in rank 0's shared memory) and pulls problems from the atomic queue.
-// Large problems of an uneven batch then get K SMs' bandwidth instead of one.
-__device__ __forceinline__ unsigned pm_cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned pm_cluster_size() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned pm_cluster_id() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void pm_cluster_arrive_wait() {   // full cluster barrier (hardware)
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-template <class T>
-__device__ __forceinline__ T* pm_map_rank(T* p, unsigned rank) {   // generic address of p in CTA rank's smem
-  T* q;
-  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(q) : "l"(p), "r"(rank));
-  return q;
-}
-
-template <class S>
-__global__ void __launch_bounds__(PM_THREADS, 1)
-k_solve_cluster(const DevProblem* probs, const int* order, int count, DevParams prm, DevResult* res,
-                unsigned char* slots, SlotLayout lay, int* queue, double* partials, int* err) {
-  extern __shared__ __align__(16) unsigned char pm_smem[];
-  PmShared& s = *reinterpret_cast<PmShared*>(pm_smem);
-  __shared__ unsigned long long s_bar;
-  __shared__ int s_next;
-  const unsigned rank = pm_cluster_rank(), K = pm_cluster_size(), cid = pm_cluster_id();
-  if (threadIdx.x == 0) {
-    s_bar = 0;
-    s_next = 0;
-  }
-  pm_cluster_arrive_wait();            // every CTA's counter initialised before remote use
-  ClusterTeam team{pm_map_rank(&s_bar, 0), err, prm.timeout_cycles, (int)rank, (int)K, 0ull};
-  const int* next0 = pm_map_rank(&s_next, 0);
-  unsigned char* base = slots + (size_t)cid * lay.bytes;
-  PmWork w{partials + (size_t)cid * 2 * K * PM_PSTRIDE, (double*)(base + lay.e_off)};
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) s_next = atomicAdd(queue, 1);
-    if (!team.sync()) break;
-    const int q = *((volatile const int*)next0);
-    if (!team.sync()) break;           // read before rank 0 takes the next problem
-    if (q >= count) break;
-    const int id = order[q];
-    DevProblem P = probs[id];
-    P.V = base + lay.v_off;
-    P.W = (double*)(base + lay.w_off);
-    P.Y = base + lay.y_off;
-    P.ld = lay.ld;
-    phipm_device<ClusterTeam, S>(team, P, prm, res[id], s, w);
-    if (rank == 0 && threadIdx.x == 0) {
-      const int e = *((volatile int*)err);
-      if (e != 0 && res[id].status == PM_OK) res[id].status = e;
-    }
-  }
-  pm_cluster_arrive_wait();            // no CTA leaves while others may still read rank 0's memory
-}
-
 // CSR values converted for the FP32 basis (valf) or the float-pair basis (val2);
 // blockIdx.y selects the problem, blockIdx.x strides over its values.
 __global__ void k_convert_values(const DevProblem* probs, int count, int mode) {
@@ -258,53 +148,30 @@ static bool params_ok(const phipm_params& p, std::string& why) {
 
 template <class S>
 static cudaError_t setup_kernels(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_solve_grid<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = pm_grid_setup<S>(smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_solve_cluster<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = pm_cluster_setup<S>(smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_solve_queue<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return pm_queue_setup<S>(smem);
 }
 
-// Cluster launch of the batched form: K CTAs per team, `clusters` teams.
-template <class S>
-static cudaError_t launch_cluster(int K, int clusters, cudaStream_t stream, const DevProblem* probs, const int* order,
-                                  int count, const DevParams& prm, DevResult* res, unsigned char* slots,
-                                  const SlotLayout& lay, int* queue, double* partials, int* err) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * K));
-  cfg.blockDim = dim3(PM_THREADS);
-  cfg.dynamicSmemBytes = sizeof(PmShared);
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)K;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_solve_cluster<S>, probs, order, count, prm, res, slots, lay, queue, partials, err);
+// Co-resident clusters of K CTAs for the precision (0 when the GPU cannot hold one).
+static int cluster_capacity(int precision, int K) {
+  const int smem = (int)sizeof(PmShared);
+  if (precision == PHIPM_F32_MIXED) return pm_cluster_capacity<float>(K, smem);
+  if (precision == PHIPM_F64_PAIR) return pm_cluster_capacity<df32>(K, smem);
+  return pm_cluster_capacity<double>(K, smem);
 }
 
-// Co-resident clusters of K CTAs (0 when the GPU cannot hold one).
-template <class S>
-static int cluster_capacity(int K) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)K);
-  cfg.blockDim = dim3(PM_THREADS);
-  cfg.dynamicSmemBytes = sizeof(PmShared);
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)K;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_solve_cluster<S>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
+static cudaError_t launch_cluster_any(int precision, int K, int clusters, cudaStream_t stream, const DevProblem* probs,
+                                      const int* order, int count, const DevParams& prm, DevResult* res,
+                                      unsigned char* slots, const SlotLayout& lay, int* queue, double* partials,
+                                      int* err) {
+  if (precision == PHIPM_F32_MIXED)
+    return pm_cluster_launch<float>(K, clusters, stream, probs, order, count, prm, res, slots, lay, queue, partials, err);
+  if (precision == PHIPM_F64_PAIR)
+    return pm_cluster_launch<df32>(K, clusters, stream, probs, order, count, prm, res, slots, lay, queue, partials, err);
+  return pm_cluster_launch<double>(K, clusters, stream, probs, order, count, prm, res, slots, lay, queue, partials, err);
 }
 
 extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* params) {
@@ -327,10 +194,7 @@ extern "C" phipm_status phipm_create(phipm_handle** out, const phipm_params* par
     delete h;
     return PHIPM_ECUDA;
   }
-  int occ[3] = {0, 0, 0};
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_solve_grid<double>, PM_THREADS, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_solve_grid<float>, PM_THREADS, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_solve_grid<df32>, PM_THREADS, smem);
+  const int occ[3] = {pm_grid_occupancy<double>(smem), pm_grid_occupancy<float>(smem), pm_grid_occupancy<df32>(smem)};
   for (int i = 0; i < 3; ++i) h->grid_blocks[i] = std::max(1, occ[i]) * h->num_sms;
   if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem)) !=
       cudaSuccess) {
@@ -522,30 +386,21 @@ static SlotLayout slot_layout(long long nmax, int pmax, int m_max, size_t es) {
   return lay;
 }
 
-template <class S>
-static cudaError_t launch_queue(int blocks, cudaStream_t stream, const DevProblem* probs, const int* order, int count,
-                                const DevParams& prm, DevResult* res, unsigned char* slots, const SlotLayout& lay,
-                                int* queue) {
-  k_solve_queue<S><<<blocks, PM_THREADS, sizeof(PmShared), stream>>>(probs, order, count, prm, res, slots, lay, queue);
-  return cudaGetLastError();
-}
-
 static cudaError_t launch_queue_any(int precision, int blocks, cudaStream_t stream, const DevProblem* probs,
                                     const int* order, int count, const DevParams& prm, DevResult* res,
                                     unsigned char* slots, const SlotLayout& lay, int* queue) {
   if (precision == PHIPM_F32_MIXED)
-    return launch_queue<float>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+    return pm_queue_launch<float>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
   if (precision == PHIPM_F64_PAIR)
-    return launch_queue<df32>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
-  return launch_queue<double>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+    return pm_queue_launch<df32>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
+  return pm_queue_launch<double>(blocks, stream, probs, order, count, prm, res, slots, lay, queue);
 }
 
 static int queue_occupancy(int precision) {
-  int occ = 1;
-  const void* f = precision == PHIPM_F32_MIXED ? (const void*)k_solve_queue<float>
-                  : precision == PHIPM_F64_PAIR ? (const void*)k_solve_queue<df32>
-                                                : (const void*)k_solve_queue<double>;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, PM_THREADS, sizeof(PmShared));
+  const int smem = (int)sizeof(PmShared);
+  const int occ = precision == PHIPM_F32_MIXED ? pm_queue_occupancy<float>(smem)
+                  : precision == PHIPM_F64_PAIR ? pm_queue_occupancy<df32>(smem)
+                                                : pm_queue_occupancy<double>(smem);
   return std::max(1, occ);
 }
 
@@ -669,9 +524,7 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
   // memory); larger teams as a cooperative grid
   int cK = 0;
   if (team >= 2 && team <= 8) {
-    cK = prec == PHIPM_F32_MIXED ? cluster_capacity<float>(team)
-         : prec == PHIPM_F64_PAIR ? cluster_capacity<df32>(team)
-                                  : cluster_capacity<double>(team);
+    cK = cluster_capacity(prec, team);
     cK = cK >= 1 ? team : 0;
   }
   if (team >= 2 && cK == 0) {
@@ -698,12 +551,10 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
     int* err = (int*)((char*)h->sync.p + 1024);
     if ((e = cudaMemsetAsync(h->sync.p, 0, 2048, stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
     if ((e = cudaMemsetAsync(res_d, 0, sizeof(DevResult), stream)) != cudaSuccess) return cuda_fail(h, e, "memset");
-    void* args[] = {(void*)&P, (void*)&prm, (void*)&res_d, (void*)&w, (void*)&bar, (void*)&err};
-    const void* fn = prec == PHIPM_F32_MIXED ? (const void*)k_solve_grid<float>
-                     : prec == PHIPM_F64_PAIR ? (const void*)k_solve_grid<df32>
-                                              : (const void*)k_solve_grid<double>;
     cudaEventRecord(h->ev0, stream);
-    e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PM_THREADS), args, sizeof(PmShared), stream);
+    e = prec == PHIPM_F32_MIXED ? pm_grid_launch<float>(G, stream, P, prm, res_d, w, bar, err)
+        : prec == PHIPM_F64_PAIR ? pm_grid_launch<df32>(G, stream, P, prm, res_d, w, bar, err)
+                                 : pm_grid_launch<double>(G, stream, P, prm, res_d, w, bar, err);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch");
     cudaEventRecord(h->ev1, stream);
   } else {
@@ -737,9 +588,7 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
       unsigned char* ws = (unsigned char*)h->ws.p;
       double* pt = (double*)h->partials.p;
       int* err = (int*)((char*)h->sync.p + 1024);
-      if (prec == PHIPM_F32_MIXED) e = launch_cluster<float>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
-      else if (prec == PHIPM_F64_PAIR) e = launch_cluster<df32>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
-      else e = launch_cluster<double>(cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
+      e = launch_cluster_any(prec, cK, 1, stream, pd, od, 1, prm, res_d, ws, lay, queue, pt, err);
     } else {
       e = launch_queue_any(prec, 1, stream, (const DevProblem*)h->probs.p, (const int*)h->order.p, 1, prm, res_d,
                            (unsigned char*)h->ws.p, lay, queue);
@@ -887,9 +736,7 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   }
   int clusters = 0;
   if (K >= 2) {
-    clusters = prec == PHIPM_F32_MIXED ? cluster_capacity<float>(K)
-               : prec == PHIPM_F64_PAIR ? cluster_capacity<df32>(K)
-                                        : cluster_capacity<double>(K);
+    clusters = cluster_capacity(prec, K);
     if (clusters < 1) K = 1;
   }
   if (K < 2) K = 1;
@@ -954,9 +801,7 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
       DevResult* rd = (DevResult*)h->res.p;
       unsigned char* ws = (unsigned char*)h->ws.p;
       double* pt = (double*)h->partials.p;
-      if (prec == PHIPM_F32_MIXED) launch_cluster<float>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
-      else if (prec == PHIPM_F64_PAIR) launch_cluster<df32>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
-      else launch_cluster<double>(K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
+      launch_cluster_any(prec, K, slots, gs, pd, od, count, prm, rd, ws, lay, queue, pt, err);
     } else {
       launch_queue_any(prec, slots, gs, (const DevProblem*)h->probs.p, (const int*)h->order.p, count, prm,
                        (DevResult*)h->res.p, (unsigned char*)h->ws.p, lay, queue);
