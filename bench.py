@@ -35,26 +35,33 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "convdiff2d_512": dict(metric_cfg="FP64 nonsymmetric (Arnoldi) convection-diffusion 512x512 CSR, p=4",
-                           precision="f64pair"),
-    "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64pair"),
+                           precision="f64", extras=["f64pair"]),
+    "laplacian2d_32": dict(metric_cfg="plain FP64 32x32 Laplacian stencil, p=3 (Lanczos)", precision="f64",
+                           extras=["f64pair"]),
     "laplacian3d_128": dict(metric_cfg="FP32-basis 128^3 Laplacian stencil, p=2, tol 1e-5", precision="f32"),
     "heston_100x51": dict(metric_cfg="Heston PDE (Sec. 4.1), 100x51 grid, n 5100, u' = Au + b_1, T = 1, tol 1e-4",
-                          precision="f64pair"),
+                          precision="f64", extras=["f64pair"]),
     "ninepoint30_phi4": dict(metric_cfg="nine-point 30x30 matrix (n 900, nnz 7,744), sum of t^k phi_k(tA) 1, "
-                                        "k <= 4, t = 2, tol 2^-26 (Sec. 4.2, Experiment 2), phipm", precision="f64pair"),
+                                        "k <= 4, t = 2, tol 2^-26 (Sec. 4.2, Experiment 2), phipm", precision="f64",
+                             extras=["f64pair"]),
     "ninepoint30_phi4_phip": dict(metric_cfg="the same problem with the fixed-dimension variant phip (m = 30)",
-                                  precision="f64pair", params=dict(controller=2, m_init=30)),
+                                  precision="f64", extras=["f64pair"], params=dict(controller=2, m_init=30)),
     "batched_convdiff_256": dict(metric_cfg="256 independent convection-diffusion problems, sides U{64..256}, "
                                             "p U{1..4}, tol 1e-8, one persistent launch replayed as a CUDA graph",
-                                 precision="f64pair", batched=True),
+                                 precision="f64", batched=True, extras=["f64pair", "f32"]),
     "batched_convdiff_256_f32": dict(metric_cfg="the same 256 problems with an FP32 Krylov basis, tol 1e-5",
                                      precision="f32", batched=True, tol=1e-5),
     "peclet_128_1024_learned": dict(metric_cfg="1024 held-out convection-diffusion 128x128 problems, Peclet "
                                                "log-uniform [1,1e3], tol 1e-8, learned (tau, m) controller",
-                                    precision="f64pair", batched=True, learned=True),
+                                    precision="f64", batched=True, learned=True, extras=["f64pair"]),
 }
 DTYPES = {"f64": "f64", "f32": "f32 basis (FP64 coefficients, H, expm, eps, u)",
           "f64pair": "f32x2 float pairs on the FP32 pipe (FP64-class; FP64 w-recurrence, H, expm, eps, u)"}
+# tolerance of each precision form when it runs as another form of a workload
+EXTRA_TOL = {"f32": 1e-5}
+KERNEL_ELEM = {"f64": "<double>", "f32": "<float>", "f64pair": "<df32>"}
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (maximum SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 METRIC = "solves/s at rel.err<=1e-8 vs FP64 oracle; SpMV+Arnoldi HBM GB/s vs peak"
 PEAK_FALLBACK = 6800.0
 
@@ -148,6 +155,19 @@ def algorithmic_bytes(pr, stats, precision) -> float:
         per_step = spmv + s * n * (2 + 4) + s * n
         return kry * per_step
     return 2.0 * s * n * gs + kry * (spmv + 6.0 * s * n)
+
+
+def fp64_flops(pr, stats) -> float:
+    """FP64 flops of one solve's Krylov phase with the IEEE FP64 basis: an Arnoldi step j
+    takes 2 j n fused multiply-adds in the dot pass (V^T z, V^T w) and 2 j n in the fused
+    update (z - V a, w - V b), plus one SpMV (nnz) and the finishing scalings (4 n); a
+    Lanczos step takes 3 n + 2 n (dot, three-term update) + nnz + 2 n (norm, scaling)."""
+    n = pr.n
+    nnz = pr.op.nnz if hasattr(pr.op, "rowptr") else pr.op.nnz()
+    kry, gs = stats["krylov_steps"], stats["gs_vectors"]
+    if gs == 0:
+        return 2.0 * kry * (nnz + 7.0 * n)
+    return 2.0 * (4.0 * n * gs + kry * (nnz + 4.0 * n))
 
 
 class ClockSampler:
@@ -446,13 +466,36 @@ def run_batched(args, world, rank, local):
                  "sample": f"{len(sample)} problems (every {max(1, count // 32)}th), one phipm_solve each, "
                            f"FP64 basis, same tol"}
 
-    peak, peak_kind = measured_peaks()
-    abytes = sum(algorithmic_bytes(pr, st, prec) for pr, st in zip(probs, stats))
-    achieved = abytes / (kernel_ms / 1e3) / 1e9
-    traffic = traffic_from_profiles("k_solve_queue", args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_solve_queue",
-                "algorithmic_bytes_per_launch": abytes, "kernel_ms": kernel_ms}
+    team = solver.last_batched_team()
+    roofline = roofline_batched(probs, stats, prec, kernel_ms, team, args.workload)
+
+    # the other precision modes of the same batch, timed the same way (not the headline)
+    extras, u_extra = {}, {}
+    for xp in spec.get("extras", []):
+        sx = pm.Phipm(xp)
+        if learned is not None:
+            sx.set_controller_weights(blob)
+            sx.set_controller(1)
+        tolx = EXTRA_TOL.get(xp)
+        outs_x = [torch.empty_like(x) for x in pk.outs]
+        bx = sx.batch([pr.t_end for pr in probs], pk.ops, pk.bs, [tolx or pr.tol for pr in probs],
+                      [pr.symm for pr in probs], outs=outs_x)
+        for _ in range(args.warmup):
+            bx.run(stream)
+        torch.cuda.synchronize()
+        xt = time_batch(bx, stream, flush, args.steps)
+        xst = bx.stats()
+        xtot = max_over_ranks(sum(xt), dist, "cuda")
+        tx = sx.last_batched_team()
+        extras[xp] = {"value": replica_throughput(count * args.steps, world, xtot), "unit": "solves/s",
+                      "ms_per_step": xtot / args.steps, "dtype": DTYPES[xp], "tol": tolx or probs[0].tol,
+                      "team": tx,
+                      "solver_stats": {k: int(sum(x[k] for x in xst)) for k in ("steps", "rejects", "krylov_steps",
+                                                                                 "gs_vectors")},
+                      "roofline": roofline_batched(probs, xst, xp, xst[0]["kernel_ms"], tx, args.workload)}
+        u_extra[xp] = [x.cpu().numpy() for x in outs_x]
+        del bx
+        sx.close()
     sizes = [pr.n for pr in probs]
     convert = prec != "f64"
     line = {
@@ -464,6 +507,7 @@ def run_batched(args, world, rank, local):
                    "n_total": int(sum(sizes)), "tol": probs[0].tol,
                    "l2": "flushed between timed batches (256 MiB write)",
                    "launch": "one persistent queue kernel per batch, replayed from a captured CUDA graph",
+                   "team": team,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "solver_stats": {k: int(sum(x[k] for x in stats)) for k in ("steps", "rejects", "matvecs", "expms",
                                                                      "krylov_steps", "gs_vectors")},
@@ -472,6 +516,8 @@ def run_batched(args, world, rank, local):
         "clocks": clocks,
         "plain_fp64_gpu_solver": plain_f64,
     }
+    if extras:
+        line["other_precisions"] = extras
     if learned is not None:
         line["learned"] = learned
         line["plain_controller"] = plain
@@ -483,19 +529,41 @@ def run_batched(args, world, rank, local):
         csample = list(range(0, count, max(1, count // 48)))[:48]
         with tempfile.TemporaryDirectory() as td:
             wall, cores, paths, res = run_oracle_pool(args.workload, csample, td)
-            errs = []
-            for i, pth in zip(csample, paths):
-                ur = np.load(pth)
-                errs.append(float(np.linalg.norm(u_gpu[i] - ur) / np.linalg.norm(ur)))
+            u_ref = {i: np.load(pth) for i, pth in zip(csample, paths)}
+
+        def rel_errs(us):
+            return [float(np.linalg.norm(us[i] - ur) / np.linalg.norm(ur)) for i, ur in u_ref.items()]
+        errs = rel_errs(u_gpu)
         line["cpu_baseline"] = {"value": len(csample) / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{len(csample)} of the {count} problems (evenly spaced), one FP64 "
                                           f"oracle solve each, spread over {cores} spawned processes"}
         line["rel_err_vs_oracle"] = {"max": max(errs), "median": statistics.median(errs), "problems": len(errs)}
+        for xp, ux in u_extra.items():       # against the oracle at the headline's tolerance
+            xe = rel_errs(ux)
+            extras[xp]["rel_err_vs_oracle"] = {"max": max(xe), "median": statistics.median(xe), "problems": len(xe)}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def roofline_batched(probs, stats, prec, kernel_ms, team, workload) -> dict:
+    """Algorithmic SpMV + Arnoldi bytes of every problem of the batch over the batched
+    kernel's event-timed duration, against the measured copy bandwidth."""
+    peak, peak_kind = measured_peaks()
+    abytes = sum(algorithmic_bytes(pr, st, prec) for pr, st in zip(probs, stats))
+    achieved = abytes / (kernel_ms / 1e3) / 1e9
+    kernel_name = ("k_solve_cluster" if team >= 2 else "k_solve_queue") + KERNEL_ELEM[prec]
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic_from_profiles(kernel_name, workload), "peak_kind": peak_kind, "kernel": kernel_name,
+           "algorithmic_bytes_per_launch": abytes, "kernel_ms": kernel_ms}
+    if prec == "f64":
+        fl = sum(fp64_flops(pr, st) for pr, st in zip(probs, stats))
+        out["fp64_pipe"] = {"achieved": fl / (kernel_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": fl / (kernel_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, "flops_per_launch": fl,
+                            "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
+    return out
 
 
 class PackedBatch:
@@ -602,17 +670,19 @@ def main():
 
     pr = make_problem(args.workload)
     spec = WORKLOADS[args.workload]
-    solver = pm.Phipm(spec["precision"], **spec.get("params", {}))
+    prec = spec["precision"]
     A = pm.DeviceOperator(pr.op)
     b = [torch.as_tensor(x).cuda() for x in pr.b]
     u = torch.empty(pr.n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    is_csr = hasattr(pr.op, "rowptr")
 
+    solver = pm.Phipm(prec, **spec.get("params", {}))
     tune = None
     if not args.no_autotune:     # untimed: picks the team size for this size class
         tune = solver.autotune(pr.t_end, A, b, pr.tol, pr.symm, out=u)
-    team = solver.team_for(0 if hasattr(pr.op, "rowptr") else 1, pr.n)
+    team = solver.team_for(0 if is_csr else 1, pr.n)
     for _ in range(args.warmup):
         solver.solve(pr.t_end, A, b, pr.tol, pr.symm, out=u)
     torch.cuda.synchronize()
@@ -622,17 +692,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    times, kms, stats = [], [], None
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, stats, _ = solver.solve(pr.t_end, A, b, pr.tol, pr.symm, out=u)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        kms.append(stats["kernel_ms"])
+    times, kms, stats = time_solves(solver, pr, A, b, u, flush, stream, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -646,7 +706,7 @@ def main():
     if not args.no_e2e:
         hostA = pm.HostOperator(pr.op)
         pinned = []
-        if hasattr(pr.op, "rowptr"):
+        if is_csr:
             for arr in (hostA.rowptr, hostA.colind, hostA.values):
                 pt = torch.from_numpy(arr).pin_memory()
                 pinned.append(pt)
@@ -671,30 +731,44 @@ def main():
         e2e = {"value": replica_throughput(args.steps, world, tot), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    peak, peak_kind = measured_peaks()
-    kernel_ms = statistics.mean(kms)
-    abytes = algorithmic_bytes(pr, stats, spec["precision"])
-    achieved = abytes / (kernel_ms / 1e3) / 1e9
-    kernel_name = "k_solve_grid" if team >= 2 else "k_solve_queue"
-    traffic = traffic_from_profiles(kernel_name, args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
-                "algorithmic_bytes_per_launch": abytes, "kernel_ms": kernel_ms}
+    roofline = roofline_single(pr, stats, prec, statistics.mean(kms), team, args.workload)
+
+    # the other precision modes of the same workload, timed the same way (not the headline)
+    extras, u_extra = {}, {}
+    for xp in spec.get("extras", []):
+        sx = pm.Phipm(xp, **spec.get("params", {}))
+        ux = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+        if not args.no_autotune:
+            sx.autotune(pr.t_end, A, b, pr.tol, pr.symm, out=ux)
+        tx = sx.team_for(0 if is_csr else 1, pr.n)
+        for _ in range(args.warmup):
+            sx.solve(pr.t_end, A, b, pr.tol, pr.symm, out=ux)
+        torch.cuda.synchronize()
+        xt, xk, xs = time_solves(sx, pr, A, b, ux, flush, stream, args.steps)
+        xtot = max_over_ranks(sum(xt), dist, "cuda")
+        extras[xp] = {"value": replica_throughput(args.steps, world, xtot), "unit": "solves/s",
+                      "ms_per_step": xtot / args.steps, "dtype": DTYPES[xp], "team": tx,
+                      "solver_stats": {k: xs[k] for k in ("steps", "rejects", "krylov_steps", "gs_vectors")},
+                      "roofline": roofline_single(pr, xs, xp, statistics.mean(xk), tx, args.workload)}
+        u_extra[xp] = ux.cpu().numpy()
+        sx.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[spec["precision"]],
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
         "data": "synthetic (seeded counter-based generator; same inputs as the oracle)",
-        "config": {"workload": args.workload, "n": pr.n, "nnz": int(pr.op.nnz if hasattr(pr.op, "rowptr") else pr.op.nnz()),
+        "config": {"workload": args.workload, "n": pr.n, "nnz": int(pr.op.nnz if is_csr else pr.op.nnz()),
                    "p": pr.p, "t_end": pr.t_end, "tol": pr.tol, "l2": "flushed between timed solves (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "team": team, "autotune_ms": {str(t): round(ms, 3) for t, ms in tune} if tune else None},
         "solver_stats": {k: stats[k] for k in ("steps", "rejects", "matvecs", "expms", "krylov_steps", "gs_vectors")},
-        "gpu_launches": args.steps * (2 if (spec["precision"] != "f64" and hasattr(pr.op, "rowptr")) else 1),
+        "gpu_launches": args.steps * (2 if (prec != "f64" and is_csr) else 1),
         "roofline": roofline,
         "clocks": clocks,
     }
+    if extras:
+        line["other_precisions"] = extras
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
@@ -706,11 +780,52 @@ def main():
                                 "sample": "one full solve of the same seeded workload (FP64 numpy/scipy oracle, "
                                           "single-threaded BLAS)"}
         line["rel_err_vs_oracle"] = float(np.linalg.norm(u_gpu - u_ref) / np.linalg.norm(u_ref))
+        for xp, ux in u_extra.items():
+            extras[xp]["rel_err_vs_oracle"] = float(np.linalg.norm(ux - u_ref) / np.linalg.norm(u_ref))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_solves(solver, pr, A, b, u, flush, stream, steps):
+    """Event-timed full solves on resident inputs, L2 flushed before each; returns the
+    per-solve times (ms), the solver kernel's own times (ms) and the last solve's stats."""
+    import torch
+    times, kms, stats = [], [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, stats, _ = solver.solve(pr.t_end, A, b, pr.tol, pr.symm, out=u)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        kms.append(stats["kernel_ms"])
+    return times, kms, stats
+
+
+def roofline_single(pr, stats, prec, kernel_ms, team, workload) -> dict:
+    """The solver kernel's algorithmic SpMV + Arnoldi bytes over its event-timed duration,
+    against the measured copy bandwidth; for the IEEE FP64 basis also its FP64 arithmetic
+    (Gram-Schmidt and SpMV fused multiply-adds) against the FP64 pipe's peak."""
+    peak, peak_kind = measured_peaks()
+    abytes = algorithmic_bytes(pr, stats, prec)
+    achieved = abytes / (kernel_ms / 1e3) / 1e9
+    kernel_name = ("k_solve_grid" if team >= 9 else "k_solve_cluster" if team >= 2 else "k_solve_queue") + \
+        KERNEL_ELEM[prec]
+    traffic = traffic_from_profiles(kernel_name, workload)
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel_name,
+           "algorithmic_bytes_per_launch": abytes, "kernel_ms": kernel_ms}
+    if prec == "f64":
+        fl = fp64_flops(pr, stats)
+        out["fp64_pipe"] = {"achieved": fl / (kernel_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": fl / (kernel_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                            "flops_per_launch": fl, "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz"}
+    return out
 
 
 if __name__ == "__main__":

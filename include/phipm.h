@@ -44,7 +44,9 @@ typedef enum {
   PHIPM_EMAXSTEPS = 5,    /* params.max_steps or params.max_rejects exceeded       */
   PHIPM_ETIMEOUT = 6,     /* a bounded device-side wait gave up                    */
   PHIPM_EBOUNDS = 7,      /* a device-side bounds check failed                     */
-  PHIPM_ETOOLARGE = 8     /* problem larger than phipm_solve_noalloc's static scratch */
+  PHIPM_ETOOLARGE = 8,    /* problem larger than phipm_solve_noalloc's static scratch */
+  PHIPM_ENOTRUN = 9       /* batched: the launch stopped (another problem's error) before
+                             this problem was solved; its u is not valid               */
 } phipm_status;
 
 typedef enum {
@@ -268,10 +270,16 @@ phipm_status phipm_mlp_train(phipm_handle* h, float* w, float* m, float* v, cons
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array, which keeps the last
- * call's contents (the kernel clears what must start at zero): calls whose work
- * overlaps on the GPU, e.g. on two streams at once, race on it and must be
- * serialised by the caller.  The call synchronises the stream before returning. */
+ * any stream capture.  With CUDA's lazy module loading (the default), that lookup
+ * is also when the device first sets the array aside, so a caller that reserves
+ * all device memory up front should make one call per device before reserving
+ * it (or run with CUDA_MODULE_LOADING=EAGER).  The address is then kept per
+ * device for the life of the process: do not reset the device
+ * (cudaDeviceReset) or replace its primary context between calls.  All calls
+ * share the one array, which keeps the last call's contents (the kernel clears
+ * what must start at zero): calls whose work overlaps on the GPU, e.g. on two
+ * streams at once, race on it and must be serialised by the caller.  The call
+ * synchronises the stream before returning. */
 #define PHIPM_NOALLOC_MAX_N 8192
 phipm_status phipm_solve_noalloc(double t_end, const phipm_operator* A, int32_t p, const double* const* b,
                                  double tol, int32_t symm, double* u, phipm_stats* stats, void* stream);
@@ -313,6 +321,9 @@ phipm_status phipm_autotune(phipm_handle* h, double t_end, const phipm_operator*
 phipm_status phipm_set_team(phipm_handle* h, int32_t team);
 /* The team size a solve of this shape would use now (0 for invalid arguments). */
 int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n);
+/* CTAs per problem (the cluster size K; 1 = one CTA per problem) of the last
+ * phipm_solve_batched call on this handle; 0 before the first. */
+int32_t phipm_batched_team(const phipm_handle* h);
 /* Save / load the tuned table as JSON: {"sms": S, "entries": [{"precision": P,
  * "kind": K, "log2n": L, "team": G, "ms": T}, ...]}.  Loading merges the entries
  * into the handle's table when S equals this GPU's SM count and ignores the file

@@ -106,6 +106,7 @@ struct phipm_handle {
   // autotuner or a loaded cache; team_force overrides (0 = use the table / default)
   std::map<int, std::pair<int, double>> tuned;
   int team_force = 0;
+  int last_batch_team = 0;           // cluster size K of the last batched launch
 };
 
 static phipm_status fail(phipm_handle* h, phipm_status st, const std::string& msg) {
@@ -345,6 +346,7 @@ static phipm_status map_status(int s) {
     case PM_EMAXSTEPS: return PHIPM_EMAXSTEPS;
     case PM_ETIMEOUT: return PHIPM_ETIMEOUT;
     case PM_EBOUNDS: return PHIPM_EBOUNDS;
+    case PM_ENOTRUN: return PHIPM_ENOTRUN;
     default: return PHIPM_ECUDA;
   }
 }
@@ -359,6 +361,8 @@ static const char* status_text(phipm_status s) {
     case PHIPM_EMAXSTEPS: return "step or reject limit exceeded";
     case PHIPM_ETIMEOUT: return "a device-side wait timed out";
     case PHIPM_EBOUNDS: return "device bounds check failed";
+    case PHIPM_ETOOLARGE: return "problem larger than the static scratch";
+    case PHIPM_ENOTRUN: return "not solved: the batched launch stopped before this problem";
   }
   return "unknown";
 }
@@ -740,18 +744,29 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
     if (clusters < 1) K = 1;
   }
   if (K < 2) K = 1;
+  h->last_batch_team = K;
   const int slots = K >= 2 ? std::max(1, std::min(count, clusters))
                            : std::max(1, std::min(count, queue_occupancy(prec) * h->num_sms));
   if (K >= 2 && !h->partials.ensure((size_t)slots * 2 * K * PM_PSTRIDE * sizeof(double)))
     return fail(h, PHIPM_ENOMEM, "partials");
   if (!h->ws.ensure((size_t)lay.bytes * slots)) return fail(h, PHIPM_ENOMEM, "workspace");
   const size_t pb = sizeof(DevProblem) * count, ob = sizeof(int) * count, rb = sizeof(DevResult) * count;
-  if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(pb + ob) ||
+  // pinned host staging: descriptors, queue order, and the records every result starts
+  // from (status "not run", overwritten by the solver; a problem that no team took
+  // because the launch stopped early keeps it)
+  const size_t r0 = (pb + ob + 15) & ~(size_t)15;
+  if (!h->probs.ensure(pb) || !h->order.ensure(ob) || !h->res.ensure(rb) || !h->probs_host.ensure(r0 + rb) ||
       !h->res_host.ensure(rb))
     return fail(h, PHIPM_ENOMEM, "descriptors");
   for (int i = 0; i < count; ++i) probs[i].id = i;
   memcpy(h->probs_host.p, probs.data(), pb);
   memcpy((char*)h->probs_host.p + pb, order.data(), ob);
+  {
+    DevResult init;
+    memset(&init, 0, sizeof(init));
+    init.status = PM_ENOTRUN;
+    for (int i = 0; i < count; ++i) memcpy((char*)h->probs_host.p + r0 + (size_t)i * sizeof(DevResult), &init, sizeof(init));
+  }
   DevParams prm = make_params(h->params);
   {
     const phipm_status st = attach_runtime(h, prm, stream);
@@ -788,7 +803,7 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
     cudaMemcpyAsync(h->probs.p, h->probs_host.p, pb, cudaMemcpyHostToDevice, gs);
     cudaMemcpyAsync(h->order.p, (char*)h->probs_host.p + pb, ob, cudaMemcpyHostToDevice, gs);
     cudaMemsetAsync(queue, 0, sizeof(int), gs);
-    cudaMemsetAsync(h->res.p, 0, rb, gs);
+    cudaMemcpyAsync(h->res.p, (char*)h->probs_host.p + r0, rb, cudaMemcpyHostToDevice, gs);
     if (prm.trace) cudaMemsetAsync(prm.trace_count, 0, sizeof(unsigned long long), gs);
     if (convert)
       k_convert_values<<<dim3(conv_blocks(max_nnz) / 8 + 1, count), 256, 0, gs>>>((const DevProblem*)h->probs.p,
@@ -976,6 +991,8 @@ extern "C" phipm_status phipm_set_team(phipm_handle* h, int32_t team) {
   h->team_force = team;
   return PHIPM_OK;
 }
+
+extern "C" int32_t phipm_batched_team(const phipm_handle* h) { return h ? h->last_batch_team : 0; }
 
 extern "C" int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n) {
   if (!h || precision < 0 || precision > 2 || (kind != 0 && kind != 1) || n <= 0) return 0;

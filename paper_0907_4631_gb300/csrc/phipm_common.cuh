@@ -21,6 +21,7 @@
 #define PM_EMAXSTEPS 5
 #define PM_ETIMEOUT 6
 #define PM_EBOUNDS 7
+#define PM_ENOTRUN 9      // batched: the launch stopped before a team took this problem
 
 struct DevOp {
   int kind;          // 0 CSR, 1 stencil
@@ -92,8 +93,8 @@ struct DevResult {
 // passed once it reaches k G.  Each CTA counts its own barriers (gen, thread 0),
 // so arriving takes one acquire-release atomic and waiting one acquire load per
 // poll, with no generation word and no separate fences.  The spin is bounded by
-// timeout cycles; on expiry the error word is set and every later barrier returns
-// at once (err is checked every 16 polls).
+// timeout cycles (the clock is read at every poll); on expiry the error word is set
+// and every later barrier returns within 16 polls (err is checked every 16 polls).
 __device__ __forceinline__ unsigned long long pm_atom_add_acq_rel(unsigned long long* p, unsigned long long v) {
   unsigned long long old;
   asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
@@ -116,10 +117,8 @@ __device__ __forceinline__ bool pm_grid_barrier(unsigned long long* cnt, int G, 
     if (prev + 1 < target) {
       const long long t0 = clock64();
       for (unsigned it = 1; pm_ld_acquire64(cnt) < target; ++it) {
-        if ((it & 15u) == 0) {
-          if (*((volatile int*)err) != 0) { s_fail = 1; break; }
-          if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_fail = 1; break; }
-        }
+        if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_fail = 1; break; }
+        if ((it & 15u) == 0 && *((volatile int*)err) != 0) { s_fail = 1; break; }
       }
     }
   }
@@ -172,10 +171,8 @@ __device__ __forceinline__ bool pm_cluster_barrier(unsigned long long* cnt, int 
     if (prev + 1 < target) {
       const long long t0 = clock64();
       for (unsigned it = 1; pm_ld_acquire_cluster(cnt) < target; ++it) {
-        if ((it & 15u) == 0) {
-          if (*((volatile int*)err) != 0) { s_cfail = 1; break; }
-          if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_cfail = 1; break; }
-        }
+        if (clock64() - t0 > timeout) { atomicCAS(err, 0, PM_ETIMEOUT); s_cfail = 1; break; }
+        if ((it & 15u) == 0 && *((volatile int*)err) != 0) { s_cfail = 1; break; }
       }
     }
   }

@@ -17,7 +17,7 @@ from . import build as _build
 
 c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE = range(9)
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE, ENOTRUN = range(10)
 F64, F32_MIXED, F64_PAIR = 0, 1, 2
 OP_CSR, OP_STENCIL = 0, 1
 CTRL_PAPER, CTRL_LEARNED, CTRL_FIXED_M = 0, 1, 2      # phipm_controller
@@ -127,6 +127,8 @@ def lib(build_if_needed: bool = True):
     L.phipm_set_team.restype = c_int32
     L.phipm_team_for.argtypes = [c_void_p, c_int32, c_int32, c_int32]
     L.phipm_team_for.restype = c_int32
+    L.phipm_batched_team.argtypes = [c_void_p]
+    L.phipm_batched_team.restype = c_int32
     L.phipm_tune_save.argtypes = [c_void_p, ctypes.c_char_p]
     L.phipm_tune_save.restype = c_int32
     L.phipm_tune_load.argtypes = [c_void_p, ctypes.c_char_p]
@@ -289,6 +291,10 @@ class Phipm:
 
     def team_for(self, kind: int, n: int) -> int:
         return lib().phipm_team_for(self.h, self.params.precision, int(kind), int(n))
+
+    def last_batched_team(self) -> int:
+        """CTAs per problem of the last batched call (phipm_batched_team)."""
+        return int(lib().phipm_batched_team(self.h))
 
     def tune_save(self, path: str):
         self._check(lib().phipm_tune_save(self.h, str(path).encode()))

@@ -13,6 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import phipm_oracle as O
 from paper_0907_4631_gb300 import phipm as pm
 from paper_0907_4631_gb300 import workloads as wl
 
@@ -25,20 +26,25 @@ def _dev(b):
     return [torch.as_tensor(np.ascontiguousarray(x)).cuda() for x in b]
 
 
-def test_noalloc_matches_phipm_solve_on_two_calls():
-    pr = wl.convdiff_2d_problem(N=64, p=3, t_end=1e-3, tol=1e-8, seed=2964)   # n = 4096 <= 8192
+@pytest.mark.parametrize("N", [64, 90])      # n = 4096, and n = 8100 near the 8192 limit
+def test_noalloc_matches_oracle_and_phipm_solve_on_two_calls(N):
+    pr = wl.convdiff_2d_problem(N=N, p=3, t_end=1e-3, tol=1e-8, seed=2900 + N)
     A = pm.DeviceOperator(pr.op)
     b = _dev(pr.b)
+    oracle, ost = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
     ref, ref_stats, st = pm.Phipm("f64").solve(pr.t_end, A, b, pr.tol, 0)
     assert st == pm.OK
     ref = ref.cpu().numpy()
+    assert np.linalg.norm(ref - oracle) / np.linalg.norm(oracle) <= TOL64
     for _ in range(2):                       # the static array keeps the previous call's contents
         u, stats, st = pm.solve_noalloc(pr.t_end, A, b, pr.tol, 0)
         torch.cuda.synchronize()
         assert st == pm.OK
         u = u.cpu().numpy()
+        assert np.linalg.norm(u - oracle) / np.linalg.norm(oracle) <= TOL64
         assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= TOL64
         assert stats["steps"] == ref_stats["steps"] and stats["rejects"] == ref_stats["rejects"]
+        assert stats["steps"] == ost.steps
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
