@@ -76,15 +76,18 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the library if it is missing or older than its sources; return its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, lib: str = LIB, defines: tuple = ()) -> str:
+    """Compile the library if it is missing or older than its sources; return its path.
+    lib and defines build a variant elsewhere (e.g. a phase-timer probe build with
+    defines=("-DPM_PHASE_PROBE",) into another file); the default is the product library."""
+    if lib == LIB and not defines and not force and not _stale():
         return LIB
     from concurrent.futures import ThreadPoolExecutor
-    os.makedirs(LIBDIR, exist_ok=True)
-    objdir = os.path.join(LIBDIR, f"obj{os.getpid()}")
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    objdir = os.path.join(os.path.dirname(lib), f"obj{os.getpid()}")
     os.makedirs(objdir, exist_ok=True)
-    common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+    common = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+              *defines]
     if verbose:
         common.append("-Xptxas=-v")
 
@@ -105,13 +108,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise subprocess.CalledProcessError(r.returncode, r.args)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp] + [o for o, _ in results], check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o, _ in results:
         os.unlink(o)
     os.rmdir(objdir)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

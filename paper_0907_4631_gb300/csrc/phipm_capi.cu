@@ -107,6 +107,9 @@ struct phipm_handle {
   std::map<int, std::pair<int, double>> tuned;
   int team_force = 0;
   int last_batch_team = 0;           // cluster size K of the last batched launch
+#ifdef PM_PHASE_PROBE
+  DevBuf phase;                      // probe build: clock cycles per solver phase
+#endif
 };
 
 static phipm_status fail(phipm_handle* h, phipm_status st, const std::string& msg) {
@@ -264,6 +267,9 @@ static DevParams make_params(const phipm_params& p) {
   d.trace = nullptr;
   d.trace_count = nullptr;
   d.trace_cap = 0;
+#ifdef PM_PHASE_PROBE
+  d.phase_ticks = nullptr;
+#endif
   // [13/13] Pade coefficients of e^x, c_j = (26-j)! 13! / (26! j! (13-j)!), from their closed form
   double c = 1.0;
   for (int j = 0; j <= 13; ++j) {
@@ -325,6 +331,9 @@ static DevOp make_devop(const phipm_operator* A, long long nnz_model) {
     o.nz = A->st.nz;
     o.cc = A->st.c_center;
     o.cc2 = host_split(o.cc);
+    o.quad = (o.nx % 4 == 0) ? 1 : 0;
+    o.mnx = o.nx >= 2 ? (~0ull / (unsigned long long)o.nx) + 1 : 0;
+    o.mny = o.ny >= 2 ? (~0ull / (unsigned long long)o.ny) + 1 : 0;
     for (int d = 0; d < 3; ++d) {
       o.cm[d] = A->st.c_minus[d];
       o.cp[d] = A->st.c_plus[d];
@@ -410,6 +419,13 @@ static int queue_occupancy(int precision) {
 
 // Attach the learned controller and the trace buffer of the handle to a launch.
 static phipm_status attach_runtime(phipm_handle* h, DevParams& prm, cudaStream_t stream) {
+#ifdef PM_PHASE_PROBE
+  if (!h->phase.p) {
+    if (!h->phase.ensure(PM_NPHASE * sizeof(unsigned long long))) return fail(h, PHIPM_ENOMEM, "phase timers");
+    cudaMemset(h->phase.p, 0, PM_NPHASE * sizeof(unsigned long long));
+  }
+  prm.phase_ticks = (unsigned long long*)h->phase.p;
+#endif
   if (h->params.controller == 1) {
     if (!h->has_mlp) return fail(h, PHIPM_EINVAL, "controller = 1 needs phipm_set_controller_weights");
     prm.mlp = (const float*)h->mlp_blob.p;
@@ -993,6 +1009,17 @@ extern "C" phipm_status phipm_set_team(phipm_handle* h, int32_t team) {
 }
 
 extern "C" int32_t phipm_batched_team(const phipm_handle* h) { return h ? h->last_batch_team : 0; }
+
+#ifdef PM_PHASE_PROBE
+// Probe build only: the accumulated clock cycles per solver phase (PM_NPHASE values), then zero them.
+extern "C" phipm_status phipm_probe_phase_ticks(phipm_handle* h, unsigned long long* out) {
+  if (!h || !out || !h->phase.p) return PHIPM_EINVAL;
+  if (cudaMemcpy(out, h->phase.p, PM_NPHASE * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PHIPM_ECUDA;
+  cudaMemset(h->phase.p, 0, PM_NPHASE * sizeof(unsigned long long));
+  return PHIPM_OK;
+}
+#endif
 
 extern "C" int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n) {
   if (!h || precision < 0 || precision > 2 || (kind != 0 && kind != 1) || n <= 0) return 0;

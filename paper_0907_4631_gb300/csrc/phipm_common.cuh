@@ -35,7 +35,17 @@ struct DevOp {
   int ndim, nx, ny, nz;
   double cc, cm[3], cp[3];
   df32 cc2, cm2[3], cp2[3];   // stencil coefficients as float pairs (hi alone for FP32)
+  int quad;                   // stencil with nx a multiple of 4: rows taken four at a time
+  int pad_;
+  unsigned long long mnx, mny;   // multiply-high divisors by nx and ny (pm_udiv; 0 for 1)
 };
+
+// x / d for 0 <= x < 2^32 as the high word of x * m, m = floor((2^64 - 1) / d) + 1 for
+// d >= 2: with m = 2^64 / d + e, 0 <= e < 1, x m / 2^64 = x / d + x e / 2^64 and
+// x e / 2^64 < 2^-32 < 1 / d, which never reaches the next integer.  m = 0 encodes d = 1.
+__device__ __forceinline__ unsigned pm_udiv(unsigned x, unsigned long long m) {
+  return m ? (unsigned)__umul64hi((unsigned long long)x, m) : x;
+}
 
 // One attempt record; the same layout as phipm_trace_record in include/phipm.h.
 struct TraceRec {
@@ -56,7 +66,26 @@ struct DevParams {
   TraceRec* trace;       // attempt records (device), or null
   unsigned long long* trace_count;
   long long trace_cap;
+#ifdef PM_PHASE_PROBE
+  unsigned long long* phase_ticks;   // probe build: clock cycles per solver phase (PM_NPHASE)
+#endif
 };
+
+// Phase timers, compiled in only by a probe build (-DPM_PHASE_PROBE): thread 0 of the
+// team's first CTA adds the clock cycles since its previous mark to ticks[k].
+#define PM_NPHASE 16
+#ifdef PM_PHASE_PROBE
+#define PM_MARK(k)                                                              \
+  do {                                                                          \
+    if (prm.phase_ticks && team.rank() == 0 && threadIdx.x == 0) {              \
+      const long long pm_t_now = clock64();                                     \
+      prm.phase_ticks[k] += (unsigned long long)(pm_t_now - pm_t_last);         \
+      pm_t_last = pm_t_now;                                                     \
+    }                                                                           \
+  } while (0)
+#else
+#define PM_MARK(k) do { } while (0)
+#endif
 
 struct DevProblem {
   DevOp A;

@@ -177,6 +177,10 @@ template <> struct Quad<float> {
     const float4 q = *reinterpret_cast<const float4*>(p);
     x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
   }
+  __device__ __forceinline__ void load_cg(const float* p) {   // through L2 (data other SMs wrote)
+    const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+  }
   __device__ __forceinline__ void store(float* p) const {
     *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
   }
@@ -185,6 +189,10 @@ template <> struct Quad<double> {
   double x[4];
   __device__ __forceinline__ void load(const double* p) {
     const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  }
+  __device__ __forceinline__ void load_cg(const double* p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
     x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
   }
   __device__ __forceinline__ void store(double* p) const {
@@ -196,6 +204,11 @@ template <> struct Quad<df32> {
   df32 x[4];
   __device__ __forceinline__ void load(const df32* p) {
     const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    x[0].hi = a.x; x[0].lo = a.y; x[1].hi = a.z; x[1].lo = a.w;
+    x[2].hi = b.x; x[2].lo = b.y; x[3].hi = b.z; x[3].lo = b.w;
+  }
+  __device__ __forceinline__ void load_cg(const df32* p) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p)), b = __ldcg(reinterpret_cast<const float4*>(p) + 1);
     x[0].hi = a.x; x[0].lo = a.y; x[1].hi = a.z; x[1].lo = a.w;
     x[2].hi = b.x; x[2].lo = b.y; x[3].hi = b.z; x[3].lo = b.w;
   }

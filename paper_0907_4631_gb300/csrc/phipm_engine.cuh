@@ -426,6 +426,136 @@ __device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, con
   }
 }
 
+// One stencil row from its centre value and six neighbours (zero where the
+// neighbour is outside the grid, which adds nothing), in spmv_row's order.
+template <class S>
+__device__ __forceinline__ S stencil_point(const DevOp& A, S xc, S xl, S xr, S ym, S yp, S zm, S zp) {
+  if constexpr (Elem<S>::kind == 0) {
+    double acc = A.cc * xc;
+    acc = fma(A.cm[0], xl, acc);
+    acc = fma(A.cp[0], xr, acc);
+    if (A.ndim > 1) { acc = fma(A.cm[1], ym, acc); acc = fma(A.cp[1], yp, acc); }
+    if (A.ndim > 2) { acc = fma(A.cm[2], zm, acc); acc = fma(A.cp[2], zp, acc); }
+    return acc;
+  } else if constexpr (Elem<S>::kind == 1) {
+    float acc = A.cc2.hi * xc;
+    acc = fmaf(A.cm2[0].hi, xl, acc);
+    acc = fmaf(A.cp2[0].hi, xr, acc);
+    if (A.ndim > 1) { acc = fmaf(A.cm2[1].hi, ym, acc); acc = fmaf(A.cp2[1].hi, yp, acc); }
+    if (A.ndim > 2) { acc = fmaf(A.cm2[2].hi, zm, acc); acc = fmaf(A.cp2[2].hi, zp, acc); }
+    return acc;
+  } else {
+    F2Acc acc = f2_zero();
+    f2_add_prod(acc, A.cc2, xc);
+    f2_add_prod(acc, A.cm2[0], xl);
+    f2_add_prod(acc, A.cp2[0], xr);
+    if (A.ndim > 1) { f2_add_prod(acc, A.cm2[1], ym); f2_add_prod(acc, A.cp2[1], yp); }
+    if (A.ndim > 2) { f2_add_prod(acc, A.cm2[2], zm); f2_add_prod(acc, A.cp2[2], zp); }
+    return f2_round(acc);
+  }
+}
+
+// Stencil product over this CTA's rows [lo, hi) taken as 16-byte quads of four
+// consecutive rows (nx a multiple of 4, so a quad never crosses a grid line; lo and
+// hi are multiples of 4 except hi = n, whose ragged rows take the per-row path).  Per
+// quad: the quad itself, its two x-neighbours and the quads of the y- and z-neighbour
+// lines, seven loads for four rows instead of twenty-eight, all issued before the
+// arithmetic, two quads per thread per pass for FP32 (one for the 8-byte types, whose
+// quads need twice the registers).  Row coordinates come from multiply-high
+// divisions (pm_udiv).  With CG, quads outside [lo, hi) (written by other CTAs of the
+// team) are read through L2; every quad lies wholly inside or outside, since lo, hi,
+// nx and nx ny are multiples of 4.
+template <class S, bool CG, class Epi>
+__device__ __forceinline__ void stencil_rows4_epi(const DevOp& A, const S* __restrict__ x, int lo, int hi,
+                                                  const Epi& epi) {
+  typedef Elem<S> E;
+  const int nx = A.nx, ny = A.ny, nz = A.nz, pl = nx * ny;
+  const int nq = (hi - lo) >> 2;
+  const S zero = E::zero_elem();
+  auto outside = [&](int r) { return CG && (unsigned)(r - lo) >= (unsigned)(hi - lo); };
+  auto ldq = [&](Quad<S>& q, int r, bool ok) {
+    if (!ok) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q.x[k] = zero;
+    } else if (outside(r)) {
+      q.load_cg(x + r);
+    } else {
+      q.load(x + r);
+    }
+  };
+  auto lds = [&](int r, bool ok) -> S { return !ok ? zero : outside(r) ? ld_cg(x + r) : x[r]; };
+  constexpr int U = sizeof(S) == 4 ? 2 : 1;
+  for (int q0 = threadIdx.x; q0 < nq; q0 += U * blockDim.x) {
+    Quad<S> c[U], ym[U], yp[U], zm[U], zp[U];
+    S xl[U], xr[U];
+    int rr[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int qi = q0 + u * blockDim.x;
+      act[u] = qi < nq;
+      const int r = lo + 4 * (act[u] ? qi : q0);
+      rr[u] = r;
+      const unsigned line = pm_udiv((unsigned)r, A.mnx);
+      const int ix = r - (int)line * nx;
+      int iy = 0, iz = 0;
+      if (A.ndim > 1) {
+        iz = (int)pm_udiv(line, A.mny);
+        iy = (int)line - iz * ny;
+      }
+      ldq(c[u], r, true);
+      xl[u] = lds(r - 1, ix > 0);
+      xr[u] = lds(r + 4, ix + 4 < nx);
+      ldq(ym[u], r - nx, A.ndim > 1 && iy > 0);
+      ldq(yp[u], r + nx, A.ndim > 1 && iy < ny - 1);
+      ldq(zm[u], r - pl, A.ndim > 2 && iz > 0);
+      ldq(zp[u], r + pl, A.ndim > 2 && iz < nz - 1);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!act[u]) continue;
+      Quad<S> y;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const S l = (k == 0) ? xl[u] : c[u].x[k - 1];
+        const S rgt = (k == 3) ? xr[u] : c[u].x[k + 1];
+        y.x[k] = stencil_point<S>(A, c[u].x[k], l, rgt, ym[u].x[k], yp[u].x[k], zm[u].x[k], zp[u].x[k]);
+      }
+      epi.quad(rr[u], y);
+    }
+  }
+  VecLoad<S, CG> xl{x, lo, hi};
+  for (int r = lo + 4 * nq + threadIdx.x; r < hi; r += blockDim.x) epi.row(r, spmv_row<S>(A, r, xl));
+}
+
+// epilogue of a plain product: out = (A x) * sc (scale) or A x
+template <class S>
+struct StoreScaled {
+  S* out;
+  typename Elem<S>::Coef sc;
+  bool scale;
+  __device__ __forceinline__ void quad(int r, Quad<S>& y) const {
+    if (scale) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) y.x[k] = Elem<S>::scale(y.x[k], sc);
+    }
+    y.store(out + r);
+  }
+  __device__ __forceinline__ void row(int r, S v) const { out[r] = scale ? Elem<S>::scale(v, sc) : v; }
+};
+
+template <class S, bool CG>
+__device__ __forceinline__ void stencil_rows4(const DevOp& A, const S* __restrict__ x, S* __restrict__ out,
+                                              typename Elem<S>::Coef sc, bool scale, int lo, int hi) {
+  stencil_rows4_epi<S, CG>(A, x, lo, hi, StoreScaled<S>{out, sc, scale});
+}
+
+template <class XL> struct IsVecLoad { static constexpr bool value = false; };
+template <class S, bool CG> struct IsVecLoad<VecLoad<S, CG>> {
+  static constexpr bool value = true;
+  static constexpr bool cg = CG;
+};
+
 // out[r] = (A x)[r] * sc over this CTA's rows (CSR rows two at a time per thread,
 // stencil rows two at a time too: their neighbour loads are independent, so a pass has
 // both rows' loads in flight instead of paying the load latency once per row)
@@ -443,6 +573,12 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
       if (r2 >= 0) out[r2] = scale ? E::scale(y1, sc) : y1;
     }
   } else {
+    if constexpr (IsVecLoad<XL>::value) {
+      if (A.quad) {
+        stencil_rows4<S, IsVecLoad<XL>::cg>(A, x.p, out, sc, scale, lo, hi);
+        return;
+      }
+    }
     for (int r = lo + threadIdx.x; r < hi; r += 2 * nth) {
       const int r2 = r + nth;
       const S y0 = spmv_row<S>(A, r, x);
@@ -452,6 +588,28 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
     }
   }
 }
+
+// epilogue of a w-recurrence product, Eq. (wrecurrence): w_j = A w_{j-1} +
+// sum_{l <= p-j} t^l / l! b_{j+l}, and the FP64 sum of squares of w_p
+struct WEpi {
+  double* out;
+  const double* const* b;    // b_j, b_{j+1}, ...
+  const double* tl;          // t^l / l!
+  int nl;                    // l = 0 .. nl
+  bool norm;
+  mutable double nrm;        // this thread's sum of squares
+  __device__ __forceinline__ double fin(int r, double y) const {
+    for (int l = 0; l <= nl; ++l) y = fma(tl[l], b[l][r], y);
+    if (norm) nrm = fma(y, y, nrm);
+    return y;
+  }
+  __device__ __forceinline__ void quad(int r, Quad<double>& y) const {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y.x[k] = fin(r + k, y.x[k]);
+    y.store(out + r);
+  }
+  __device__ __forceinline__ void row(int r, double v) const { out[r] = fin(r, v); }
+};
 
 // ------------------------------------------------------------------------------------
 // Gram-Schmidt passes over this CTA's rows [lo, hi)
@@ -835,11 +993,23 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
       const S* v = (i < nv) ? V + (size_t)i * ld : zb;
       typename E::Red dz, dw;
       dot_segment2<S, WIDE>(v, zb, wb, lo + (int)r0, lo + (int)r1, dz, dw);
-      dz = red_warp_sum<E>(dz);
-      dw = red_warp_sum<E>(dw);
-      if (lane == 0) {
-        red_put(&s.dred[warp * PM_DSEG + 2 * seg], dz);
-        red_put(&s.dred[warp * PM_DSEG + 2 * seg + 1], dw);
+      if constexpr (E::kind == 0) {
+        // both sums in one tree: at the first level the lower half-warp keeps z and the
+        // upper half keeps w, so five FP64 adds finish both (an FP64 warp instruction
+        // costs the same however many of its lanes are active)
+        const bool up = lane >= 16;
+        double keep = up ? dw : dz;
+        keep += __shfl_xor_sync(0xffffffffu, up ? dz : dw, 16);
+#pragma unroll
+        for (int o = 8; o; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+        if ((lane & 15) == 0) s.dred[warp * PM_DSEG + 2 * seg + (up ? 1 : 0)] = keep;
+      } else {
+        dz = red_warp_sum<E>(dz);
+        dw = red_warp_sum<E>(dw);
+        if (lane == 0) {
+          red_put(&s.dred[warp * PM_DSEG + 2 * seg], dz);
+          red_put(&s.dred[warp * PM_DSEG + 2 * seg + 1], dw);
+        }
       }
       f += r1 - r0;
     }
@@ -1317,6 +1487,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   long long matvecs = 0, kry_steps = 0, gs_vectors = 0;
   Ctl ctl;                                // thread 0's controller memory
   ctl_reset(ctl);
+#ifdef PM_PHASE_PROBE
+  long long pm_t_last = clock64();
+#endif
   for (int e = tid; e < (PM_MAXM + 1) * PM_MAXM; e += nth) s.H[e] = 0.0;
   if (tid == 0) {
     c.status = PM_OK;
@@ -1424,6 +1597,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     goto done;
   }
   PM_SYNC_OR_FAIL();  // u = b_0 complete before the first SpMV
+  PM_MARK(0);
 
   while (c.t < c.t_end) {
     // ---------------- w-recurrence (a2), Eq. (wrecurrence): p SpMVs in FP64
@@ -1435,14 +1609,14 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     for (int j = 1; j <= p; ++j) {
       const double* xin = (j == 1) ? u : W + (size_t)(j - 2) * ld;
       double* wout = W + (size_t)(j - 1) * ld;
-      double nrm = 0.0;
       VecLoad<double, Team::multi> xl{xin, lo, hi};
-      for (int r = lo + tid; r < hi; r += nth) {
-        double y = spmv_row<double>(P.A, r, xl);
-        for (int l = 0; l <= p - j; ++l) y = fma(c.tl[l], P.b[j + l][r], y);
-        wout[r] = y;
-        if (j == p) nrm = fma(y, y, nrm);
+      WEpi we{wout, P.b + j, c.tl, p - j, j == p, 0.0};
+      if (P.A.kind == 1 && P.A.quad) {
+        stencil_rows4_epi<double, Team::multi>(P.A, xin, lo, hi, we);
+      } else {
+        for (int r = lo + tid; r < hi; r += nth) we.row(r, spmv_row<double>(P.A, r, xl));
       }
+      const double nrm = we.nrm;
       matvecs += 1;
       if (j == p) {
         const double v[1] = {nrm};
@@ -1459,6 +1633,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       block_sum(s, v, 1, s.coef);
       PM_SUM_OR_FAIL(1);
     }
+    PM_MARK(1);
     if (tid == 0) {
       c.beta = sqrt(s.coef[0]);
       if (c.beta > 0.0) set_inv(c, c.beta);
@@ -1505,6 +1680,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     __syncthreads();
     const double* wp = (p == 0) ? u : W + (size_t)(p - 1) * ld;
     for (;;) {   // attempts of one step (Algorithm 3, inner loop)
+      PM_MARK(2);
       if (tid == 0) {
         c.tau_used = c.tau;
         c.m_req = c.m;
@@ -1556,8 +1732,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             kry_steps += 1;
             gs_vectors += j;
             __syncthreads();
+            PM_MARK(3);
             dots2_cta<S, !Team::multi>(V, ld, j, zp, Wv, lo, hi, s);
+            PM_MARK(4);
             PM_BSUM_OR_FAIL(2 * (j + 1));
+            PM_MARK(5);
             // scalars by one warp (||a||^2, a.b); a and b copied by every thread
             if (tid < 32) {
               double aa = 0.0, ab = 0.0;
@@ -1631,6 +1810,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               __syncthreads();
               break;
             }
+            PM_MARK(6);
             // columns j-1 (second pass, subdiagonal nu) and j (first pass) of H, row l by
             // thread l; H is next read after later barriers, so the update starts at once
             for (int l = tid; l <= j; l += nth) {
@@ -1652,7 +1832,9 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             }
             update_rows2<S>(V, ld, j, ca, cb, E::coef(c.dcoef), scal_inv<S>(c), zp, Wv,
                             zfinal ? nullptr : V + (size_t)j * ld, Z, !zfinal, lo, hi);
+            PM_MARK(7);
             PM_SYNC_OR_FAIL();                 // the next SpMV reads other CTAs' rows of the candidate
+            PM_MARK(8);
             if (tid == 0) c.kcur = j;          // complete columns 0 .. j-1
           }
           if (!c.invariant) {
@@ -1721,19 +1903,15 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             const C sc = scal_inv<S>(c);   // 1/beta at j = 0, else 1/||y_{j-1}||
             if (j == 0) {
               DLoadAs<S, Team::multi> xl{wp, lo, hi};
-              for (int r = lo + tid; r < hi; r += nth) {
-                V[r] = E::from_d(wp[r] * c.inv);
-                ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
-              }
+              for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
+              spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
             } else if (j == j0) {
               VecLoad<S, Team::multi> xl{V + (size_t)j * ld, lo, hi};   // v_j normalised at the end of the previous extension
-              for (int r = lo + tid; r < hi; r += nth) ycur[r] = spmv_row<S>(P.A, r, xl);
+              spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi);
             } else {
               VecLoad<S, Team::multi> xl{yprev, lo, hi};
-              for (int r = lo + tid; r < hi; r += nth) {
-                V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
-                ycur[r] = E::scale(spmv_row<S>(P.A, r, xl), sc);
-              }
+              for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
+              spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
             }
             matvecs += 1;
             kry_steps += 1;
@@ -1781,6 +1959,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             for (int r = lo + tid; r < hi; r += nth) V[(size_t)c.kcur * ld + r] = E::scale(yl[r], sc);
           }
         }
+        PM_MARK(9);
         // ---------------- augmented matrix (Eq. hathm + R2) and its exponential (a5)
         // ||H_hat||_1 = max(tau ||H_m||_1, 1): the augmented columns each hold a single 1
         if (tid < 32) {
@@ -1808,6 +1987,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           goto done;
         }
       }
+      PM_MARK(11);
       // ---------------- error estimate (a6) and controller (a7): thread 0
       if (tid == 0) {
         const int mu = c.m_used;
@@ -1952,6 +2132,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
         if (c.outcome != PM_ATT_ACCEPT) c.step_rejects += 1;
       }
       __syncthreads();
+      PM_MARK(12);
       if (c.outcome == PM_ATT_FAIL) goto done;
       if (c.outcome != PM_ATT_ACCEPT) continue;
       {
@@ -2019,6 +2200,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           c.step_rejects = 0;
         }
         PM_SYNC_OR_FAIL();    // u complete before the next SpMV reads neighbours; c visible
+        PM_MARK(13);
         if (c.status != PM_OK) goto done;
         break;
       }
