@@ -159,15 +159,18 @@ def algorithmic_bytes(pr, stats, precision) -> float:
 
 def fp64_flops(pr, stats) -> float:
     """FP64 flops of one solve's Krylov phase with the IEEE FP64 basis: an Arnoldi step j
-    takes 2 j n fused multiply-adds in the dot pass (V^T z, V^T w) and 2 j n in the fused
-    update (z - V a, w - V b), plus one SpMV (nnz) and the finishing scalings (4 n); a
-    Lanczos step takes 3 n + 2 n (dot, three-term update) + nnz + 2 n (norm, scaling)."""
+    takes j n fused multiply-adds in the dot pass (V^T w) and j n in the fused update
+    (w - V b), twice that when it also forms the candidate's second projection (V^T z,
+    z - V a; counted by reorth_vectors), plus one SpMV (nnz) and the finishing scalings
+    (4 n); a Lanczos step takes 3 n + 2 n (dot, three-term update) + nnz + 2 n (norm,
+    scaling)."""
     n = pr.n
     nnz = pr.op.nnz if hasattr(pr.op, "rowptr") else pr.op.nnz()
     kry, gs = stats["krylov_steps"], stats["gs_vectors"]
     if gs == 0:
         return 2.0 * kry * (nnz + 7.0 * n)
-    return 2.0 * (4.0 * n * gs + kry * (nnz + 4.0 * n))
+    reorth = stats.get("reorth_vectors", gs)
+    return 2.0 * (2.0 * n * (gs + reorth) + kry * (nnz + 4.0 * n))
 
 
 class ClockSampler:
@@ -491,7 +494,7 @@ def run_batched(args, world, rank, local):
                       "ms_per_step": xtot / args.steps, "dtype": DTYPES[xp], "tol": tolx or probs[0].tol,
                       "team": tx,
                       "solver_stats": {k: int(sum(x[k] for x in xst)) for k in ("steps", "rejects", "krylov_steps",
-                                                                                 "gs_vectors")},
+                                                                                 "gs_vectors", "reorth_vectors")},
                       "roofline": roofline_batched(probs, xst, xp, xst[0]["kernel_ms"], tx, args.workload)}
         u_extra[xp] = [x.cpu().numpy() for x in outs_x]
         del bx
@@ -510,7 +513,8 @@ def run_batched(args, world, rank, local):
                    "team": team,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "solver_stats": {k: int(sum(x[k] for x in stats)) for k in ("steps", "rejects", "matvecs", "expms",
-                                                                     "krylov_steps", "gs_vectors")},
+                                                                     "krylov_steps", "gs_vectors",
+                                                                     "reorth_vectors")},
         "gpu_launches": args.steps * (2 if convert else 1),
         "roofline": roofline,
         "clocks": clocks,
@@ -748,7 +752,8 @@ def main():
         xtot = max_over_ranks(sum(xt), dist, "cuda")
         extras[xp] = {"value": replica_throughput(args.steps, world, xtot), "unit": "solves/s",
                       "ms_per_step": xtot / args.steps, "dtype": DTYPES[xp], "team": tx,
-                      "solver_stats": {k: xs[k] for k in ("steps", "rejects", "krylov_steps", "gs_vectors")},
+                      "solver_stats": {k: xs[k] for k in ("steps", "rejects", "krylov_steps", "gs_vectors",
+                                                           "reorth_vectors")},
                       "roofline": roofline_single(pr, xs, xp, statistics.mean(xk), tx, args.workload)}
         u_extra[xp] = ux.cpu().numpy()
         sx.close()
@@ -762,7 +767,8 @@ def main():
                    "p": pr.p, "t_end": pr.t_end, "tol": pr.tol, "l2": "flushed between timed solves (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "team": team, "autotune_ms": {str(t): round(ms, 3) for t, ms in tune} if tune else None},
-        "solver_stats": {k: stats[k] for k in ("steps", "rejects", "matvecs", "expms", "krylov_steps", "gs_vectors")},
+        "solver_stats": {k: stats[k] for k in ("steps", "rejects", "matvecs", "expms", "krylov_steps", "gs_vectors",
+                                                "reorth_vectors")},
         "gpu_launches": args.steps * (2 if (prec != "f64" and is_csr) else 1),
         "roofline": roofline,
         "clocks": clocks,

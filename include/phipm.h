@@ -102,7 +102,10 @@ typedef struct {
  * completion of each extension's last vector), the number of earlier basis
  * vectors each orthogonalisation pass reads (j at step j; 0 for Lanczos steps).
  * kernel_ms is the device time of the solver kernel, from CUDA events on the
- * call's stream. */
+ * call's stream.  reorth_vectors sums j over the Arnoldi steps whose pass also
+ * formed the candidate's second projection (always with the FP32 basis; only when
+ * the first projection kept less than a quarter of the vector's norm with the
+ * FP64-class bases); those passes take two products per basis element, the others one. */
 typedef struct {
   int64_t steps;
   int64_t rejects;
@@ -112,6 +115,7 @@ typedef struct {
   int64_t krylov_steps;
   int64_t gs_vectors;
   double kernel_ms;
+  int64_t reorth_vectors;
 } phipm_stats;
 
 /* Method parameters.  phipm_default_params() gives the paper's values:

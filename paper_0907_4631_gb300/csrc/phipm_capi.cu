@@ -384,6 +384,7 @@ static void fill_stats(phipm_stats* o, const DevResult& r, float kernel_ms) {
   o->err_est_sum = r.err_est_sum;
   o->krylov_steps = r.kry_steps;
   o->gs_vectors = r.gs_vectors;
+  o->reorth_vectors = r.reorth_vectors;
   o->kernel_ms = kernel_ms;
 }
 

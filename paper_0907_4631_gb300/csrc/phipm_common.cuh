@@ -106,7 +106,7 @@ struct DevResult {
   int status;
   int symmetric;
   long long steps, rejects, matvecs, expms;
-  long long kry_steps, gs_vectors;
+  long long kry_steps, gs_vectors, reorth_vectors;
   double err_est_sum;
   double normA, normb;
   double last_tau;

@@ -11,6 +11,12 @@
 
 // FP32 basis mode: bound on ||F|| / ||u_new|| per step (F = tau^p phi_p(tau A) w_p)
 #define PM_F32_AMP 32.0
+// Selective second Gram-Schmidt pass (FP64 and float-pair bases): a candidate that
+// keeps at least sqrt(PM_ETA2) = 1/4 of its norm through the first projection is
+// orthogonal to the basis to a few units of rounding after that one projection (the
+// Daniel-Gragg-Kaufman-Stewart bound: loss at most about eps / 0.25), so its second
+// pass is skipped.  The FP32 basis always takes both passes.
+#define PM_ETA2 0.0625
 #define PM_DRED (PM_WARPS * (PM_NSLOT + 2))   // partials of a dot pass (vector x warp) or of a team fold
 #define PM_ZW_BYTES 65536                      // shared staging of the two vectors every product of a dot pass reads
 
@@ -21,6 +27,8 @@ struct PmScal {
   double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
   double fnorm, last_tau, omega, last_omega, m_new;
   double fz, fw, fab, dcoef;            // lagged Gram-Schmidt: z.z, z.w, a.b, d
+  double fww, fbb;                      // w.w and ||b||^2 (first-pass retention of the next candidate)
+  int skipz;                            // the current candidate keeps its single projection
   double tl[PM_MAXP + 1];
   df32 inv2;
   float invf;
@@ -871,9 +879,9 @@ __device__ __forceinline__ void update_rows(S* __restrict__ y, const S* __restri
 // Two dot products per left vector in one pass, for the lagged Gram-Schmidt step
 // (WIDE: more loads in flight per lane, measured faster when one CTA streams a whole
 // problem and slower for the short runs of a grid team):
-// with L_i = V_i (i < nv) and L_nv = z, s.coef[i] = L_i . z and
-// s.coef[nv + 1 + i] = L_i . w (i <= nv).  Runs per warp as in dots_cta; each
-// segment leaves two warp-reduced partials in s.dred (even / odd slots).
+// with L_i = V_i (i < nv), L_nv = z and, with_ww, L_{nv+1} = w (nvec left vectors),
+// s.coef[i] = L_i . z and s.coef[nvec + i] = L_i . w.  Runs per warp as in dots_cta;
+// each segment leaves two warp-reduced partials in s.dred (even / odd slots).
 template <class S, bool WIDE>
 __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* __restrict__ z,
                                              const S* __restrict__ w, int a, int b, typename Elem<S>::Red& dz,
@@ -945,11 +953,11 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
 
 template <class S, bool WIDE>
 __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                          const S* __restrict__ w, int lo, int hi, PmShared& s) {
+                          const S* __restrict__ w, int lo, int hi, bool with_ww, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
-  const int nvec = nv + 1;
+  const int nvec = nv + 1 + (with_ww ? 1 : 0);
   const long long total = (long long)nvec * rows;
   if (total == 0) {
     for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
@@ -990,7 +998,7 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
     long long r0 = f - (long long)i * rows;
     for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
       const long long r1 = min(rows, r0 + (fend - f));
-      const S* v = (i < nv) ? V + (size_t)i * ld : zb;
+      const S* v = (i < nv) ? V + (size_t)i * ld : (i == nv) ? zb : wb;
       typename E::Red dz, dw;
       dot_segment2<S, WIDE>(v, zb, wb, lo + (int)r0, lo + (int)r1, dz, dw);
       if constexpr (E::kind == 0) {
@@ -1029,23 +1037,92 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
   __syncthreads();
 }
 
+// The pass of an Arnoldi step whose candidate z keeps its single projection (no second
+// Gram-Schmidt pass, see the Krylov loop): one product per basis element,
+//   s.coef[i] = V_i . w (i < nv), s.coef[nv] = z.z, s.coef[nv+1] = z.w, s.coef[nv+2] = w.w,
+// as the runs of dots_cta over the nv + 3 (left, right) pairs, z and w staged in shared
+// memory when they fit.
+template <class S>
+__device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
+  typedef Elem<S> E;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long rows = hi - lo;
+  const int nvec = nv + 3;
+  const long long total = (long long)nvec * rows;
+  if (total == 0) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    __syncthreads();
+    return;
+  }
+  constexpr int VEC = 16 / sizeof(S);
+  const long long rows16 = (rows + VEC - 1) / VEC * VEC;
+  const S* zb = z;
+  const S* wb = w;
+  if (2 * rows16 * (long long)sizeof(S) <= (long long)PM_ZW_BYTES) {
+    S* sz = reinterpret_cast<S*>(s.zw);
+    S* sw = sz + rows16;
+    const int nq = (int)(rows / VEC);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      reinterpret_cast<float4*>(sz)[q] = *reinterpret_cast<const float4*>(z + lo + q * VEC);
+      reinterpret_cast<float4*>(sw)[q] = *reinterpret_cast<const float4*>(w + lo + q * VEC);
+    }
+    for (int r = nq * VEC + threadIdx.x; r < rows; r += blockDim.x) {
+      sz[r] = z[lo + r];
+      sw[r] = w[lo + r];
+    }
+    __syncthreads();
+    zb = sz - lo;
+    wb = sw - lo;
+  }
+  const long long run = (((total + PM_WARPS - 1) / PM_WARPS) + 3) & ~3ll;
+  long long f = (long long)warp * run;
+  const long long fend = min(total, f + run);
+  if (f < fend) {
+    int i = (int)(f / rows);
+    long long r0 = f - (long long)i * rows;
+    for (int seg = 0; f < fend; ++seg, ++i, r0 = 0) {
+      const long long r1 = min(rows, r0 + (fend - f));
+      const S* a = (i < nv) ? V + (size_t)i * ld : (i == nv + 2) ? wb : zb;
+      const S* b = (i == nv) ? zb : wb;
+      const typename E::Red d = red_warp_sum<E>(dot_segment<S>(a, b, lo + (int)r0, lo + (int)r1));
+      if (lane == 0) red_put(&s.dred[warp * PM_DSEG + seg], d);
+      f += r1 - r0;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    const long long fa = (long long)i * rows, fb = fa + rows - 1;
+    typename E::Red t = E::red_zero();
+    for (long long w2 = fa / run; w2 <= fb / run && w2 < PM_WARPS; ++w2)
+      t = E::red_add(t, red_get<typename E::Red>(&s.dred[w2 * PM_DSEG + (int)(i - (w2 * run) / rows)]));
+    s.coef[i] = E::red_val(t);
+  }
+  __syncthreads();
+}
+
 // Fused update of the lagged Gram-Schmidt step over this CTA's rows:
 //   q = (z - sum_{i<nv} a_i V_i) * inv                  (written to qout when qout != 0)
 //   z' = (w - sum_{i<nv} b_i V_i - d q) * inv            (written to zout when zout != 0)
-// with q = z when reorth is false (z is then the normalised basis vector itself).
-// Four consecutive rows per thread, four basis quads in flight, each loaded once for
-// both sums.  zout may alias z (each thread reads its rows of z before writing them).
+// mode PM_UPD_Q_IS_Z: q = z (z is the normalised basis vector itself); PM_UPD_SCALE:
+// q = z * inv (the candidate keeps its single projection, a = 0); PM_UPD_REORTH: as
+// above.  Four consecutive rows per thread, four basis quads in flight, each loaded
+// once for both sums.  zout may alias z (each thread reads its rows of z before
+// writing them).
+#define PM_UPD_Q_IS_Z 0
+#define PM_UPD_SCALE 1
+#define PM_UPD_REORTH 2
 template <class S>
 __device__ __forceinline__ void upd2_finish(Quad<S>& q, Quad<S>& zn, const Quad<S>& zq, const Quad<S>& wq,
-                                            typename Elem<S>::Coef d, typename Elem<S>::Coef inv, bool reorth) {
+                                            typename Elem<S>::Coef d, typename Elem<S>::Coef inv, int mode) {
   typedef Elem<S> E;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if constexpr (E::kind == 2) {
-      q.x[k] = reorth ? df_mul(q.x[k], inv) : zq.x[k];
+      q.x[k] = (mode != PM_UPD_Q_IS_Z) ? df_mul(q.x[k], inv) : zq.x[k];
       zn.x[k] = df_mul(df_sub(zn.x[k], df_mul(d, q.x[k])), inv);
     } else {
-      q.x[k] = reorth ? q.x[k] * (S)inv : zq.x[k];
+      q.x[k] = (mode != PM_UPD_Q_IS_Z) ? q.x[k] * (S)inv : zq.x[k];
       zn.x[k] = fma(-(S)d, q.x[k], zn.x[k]) * (S)inv;
     }
   }
@@ -1054,7 +1131,7 @@ __device__ __forceinline__ void upd2_finish(Quad<S>& q, Quad<S>& zn, const Quad<
 template <class S>
 __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, const typename Elem<S>::Coef* ca,
                              const typename Elem<S>::Coef* cb, typename Elem<S>::Coef d, typename Elem<S>::Coef inv,
-                             const S* z, const S* __restrict__ w, S* qout, S* zout, bool reorth, int lo, int hi) {
+                             const S* z, const S* __restrict__ w, S* qout, S* zout, int mode, int lo, int hi) {
   typedef Elem<S> E;
   for (int r = lo + 4 * threadIdx.x; r < hi; r += 4 * blockDim.x) {
     if (r + 3 < hi) {
@@ -1073,7 +1150,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
             const df32 au = ca[i + u], bu = cb[i + u];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              if (reorth) f2_add_prod(sa[k], au, v[u].x[k]);
+              if (mode == PM_UPD_REORTH) f2_add_prod(sa[k], au, v[u].x[k]);
               f2_add_prod(sb[k], bu, v[u].x[k]);
             }
           }
@@ -1084,7 +1161,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
           const df32 au = ca[i], bu = cb[i];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            if (reorth) f2_add_prod(sa[k], au, v0.x[k]);
+            if (mode == PM_UPD_REORTH) f2_add_prod(sa[k], au, v0.x[k]);
             f2_add_prod(sb[k], bu, v0.x[k]);
           }
         }
@@ -1110,7 +1187,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
             const S au = (S)ca[i + u], bu = (S)cb[i + u];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              if (reorth) q.x[k] = fma(-au, v[u].x[k], q.x[k]);
+              if (mode == PM_UPD_REORTH) q.x[k] = fma(-au, v[u].x[k], q.x[k]);
               zn.x[k] = fma(-bu, v[u].x[k], zn.x[k]);
             }
           }
@@ -1121,12 +1198,12 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
           const S au = (S)ca[i], bu = (S)cb[i];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            if (reorth) q.x[k] = fma(-au, v0.x[k], q.x[k]);
+            if (mode == PM_UPD_REORTH) q.x[k] = fma(-au, v0.x[k], q.x[k]);
             zn.x[k] = fma(-bu, v0.x[k], zn.x[k]);
           }
         }
       }
-      upd2_finish<S>(q, zn, zq, wq, d, inv, reorth);
+      upd2_finish<S>(q, zn, zq, wq, d, inv, mode);
       if (qout) q.store(qout + r);
       if (zout) zn.store(zout + r);
     } else {
@@ -1136,7 +1213,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
           F2Acc sa = f2_zero(), sb = f2_zero();
           for (int i = 0; i < nv; ++i) {
             const df32 vi = V[(size_t)i * ld + t];
-            if (reorth) f2_add_prod(sa, ca[i], vi);
+            if (mode == PM_UPD_REORTH) f2_add_prod(sa, ca[i], vi);
             f2_add_prod(sb, cb[i], vi);
           }
           zq.x[0] = z[t];
@@ -1149,7 +1226,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
           S qa = zq.x[0], zb = wq.x[0];
           for (int i = 0; i < nv; ++i) {
             const S vi = V[(size_t)i * ld + t];
-            if (reorth) qa = fma(-(S)ca[i], vi, qa);
+            if (mode == PM_UPD_REORTH) qa = fma(-(S)ca[i], vi, qa);
             zb = fma(-(S)cb[i], vi, zb);
           }
           q.x[0] = qa;
@@ -1157,7 +1234,7 @@ __device__ void update_rows2(const S* __restrict__ V, long long ld, int nv, cons
         }
 #pragma unroll
         for (int k = 1; k < 4; ++k) { q.x[k] = q.x[0]; zn.x[k] = zn.x[0]; zq.x[k] = zq.x[0]; wq.x[k] = wq.x[0]; }
-        upd2_finish<S>(q, zn, zq, wq, d, inv, reorth);
+        upd2_finish<S>(q, zn, zq, wq, d, inv, mode);
         if (qout) qout[t] = q.x[0];
         if (zout) zout[t] = zn.x[0];
       }
@@ -1171,7 +1248,7 @@ template <class S>
 __device__ __noinline__ void update_rows2_cold(const S* V, long long ld, int nv, const typename Elem<S>::Coef* ca,
                                                typename Elem<S>::Coef inv, const S* z, const S* w, S* qout,
                                                int lo, int hi) {
-  update_rows2<S>(V, ld, nv, ca, ca, Elem<S>::coef(0.0), inv, z, w, qout, nullptr, true, lo, hi);
+  update_rows2<S>(V, ld, nv, ca, ca, Elem<S>::coef(0.0), inv, z, w, qout, nullptr, PM_UPD_REORTH, lo, hi);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1484,7 +1561,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   C* hc = coef_array<S>(s);               // coefficients of the current update, as S needs them
   PmScal& c = s.sc;                       // scalar state: written by thread 0, read after a barrier
   int parity = 0;
-  long long matvecs = 0, kry_steps = 0, gs_vectors = 0;
+  long long matvecs = 0, kry_steps = 0, gs_vectors = 0, reorth_vectors = 0;
   Ctl ctl;                                // thread 0's controller memory
   ctl_reset(ctl);
 #ifdef PM_PHASE_PROBE
@@ -1639,6 +1716,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       if (c.beta > 0.0) set_inv(c, c.beta);
       c.kcur = 0;          // Arnoldi / Lanczos steps done for this w_p
       c.invariant = 0;     // happy breakdown reached
+      c.skipz = 0;
       c.hn = 0.0;          // ||y|| of the last step (h_{kcur+1,kcur})
       c.attempt = 0;
       c.source = 0;
@@ -1712,6 +1790,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           // barrier per step, against two of each for classical Gram-Schmidt applied
           // twice.  The last candidate is completed after the loop.  At the first
           // iteration of an extension the candidate is v_j itself (a = 0, nu = 1).
+          // With the FP64-class bases the second pass is selective: the pass also forms
+          // w.w and ||b||^2, which give by Pythagoras how much of w the next candidate
+          // keeps; when it keeps at least a quarter of its norm, the next step skips that
+          // candidate's second pass (a = 0) and streams the basis with one product per
+          // element (dots_skip_cta, PM_UPD_SCALE) instead of two.
           S* Z = Y;                          // candidate (own rows + halo)
           S* Wv = Y + ld;                    // A applied to the candidate
           C* ca = coef_array<S>(s);
@@ -1733,31 +1816,46 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             gs_vectors += j;
             __syncthreads();
             PM_MARK(3);
-            dots2_cta<S, !Team::multi>(V, ld, j, zp, Wv, lo, hi, s);
+            // single: z keeps its one projection (or is v_j itself): only V^T w is needed
+            const bool single = zfinal || c.skipz;
+            if (!single) reorth_vectors += j;
+            const bool with_ww = E::kind != 1;
+            int ib, izw, iww, K;                 // where b, z.w and w.w land in s.coef
+            if (single) {
+              dots_skip_cta<S>(V, ld, j, zp, Wv, lo, hi, s);
+              ib = 0; izw = j + 1; iww = j + 2; K = j + 3;
+            } else {
+              dots2_cta<S, !Team::multi>(V, ld, j, zp, Wv, lo, hi, with_ww, s);
+              const int nvec = j + 1 + (with_ww ? 1 : 0);
+              ib = nvec; izw = nvec + j; iww = nvec + j + 1; K = 2 * nvec;
+            }
             PM_MARK(4);
-            PM_BSUM_OR_FAIL(2 * (j + 1));
+            PM_BSUM_OR_FAIL(K);
             PM_MARK(5);
-            // scalars by one warp (||a||^2, a.b); a and b copied by every thread
+            // scalars by one warp (||a||^2, a.b, ||b||^2); a and b copied by every thread
             if (tid < 32) {
-              double aa = 0.0, ab = 0.0;
-              if (!zfinal)
-                for (int k = tid; k < j; k += 32) {
-                  const double ak = s.coef[k];
-                  aa = fma(ak, ak, aa);
-                  ab = fma(ak, s.coef[j + 1 + k], ab);
-                }
+              double aa = 0.0, ab = 0.0, bb = 0.0;
+              for (int k = tid; k < j; k += 32) {
+                const double ak = single ? 0.0 : s.coef[k], bk = s.coef[ib + k];
+                aa = fma(ak, ak, aa);
+                ab = fma(ak, bk, ab);
+                bb = fma(bk, bk, bb);
+              }
               aa = pm_warp_sum(aa);
               ab = pm_warp_sum(ab);
+              bb = pm_warp_sum(bb);
               if (tid == 0) {
                 c.fz = s.coef[j];                // z.z
-                c.fw = s.coef[2 * j + 1];        // z.w
+                c.fw = s.coef[izw];              // z.w
+                c.fww = with_ww ? s.coef[iww] : 0.0;   // w.w
                 c.fab = ab;                      // a.b
+                c.fbb = bb;                      // ||b||^2
                 c.hn = zfinal ? 1.0 : c.fz - aa; // nu^2 by Pythagoras
-                c.measure = (zfinal || aa <= 0.25 * c.fz) ? 0 : 1;   // else: project the candidate again
+                c.measure = (single || aa <= 0.25 * c.fz) ? 0 : 1;   // else: project the candidate again
               }
             }
             for (int k = tid; k < j; k += nth) {
-              const double ak = zfinal ? 0.0 : s.coef[k], bk = s.coef[j + 1 + k];
+              const double ak = single ? 0.0 : s.coef[k], bk = s.coef[ib + k];
               s.h1[k] = ak;
               s.hb[k] = bk;
               ca[k] = E::coef(ak);
@@ -1801,6 +1899,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               } else {
                 set_inv(c, c.hn);
                 c.dcoef = (c.fw - c.fab) * c.inv;  // d = (z.w - a.b) / nu
+                // the next candidate w - V b - d v_j keeps ||.||^2 = w.w - ||b||^2 - d^2 of
+                // w.w (Pythagoras); if that is at least PM_ETA2 w.w, one projection leaves it
+                // orthogonal to working accuracy and its second pass is skipped
+                const double keep = c.fww - c.fbb - c.dcoef * c.dcoef;
+                c.skipz = (with_ww && c.fww > 0.0 && keep >= PM_ETA2 * c.fww) ? 1 : 0;
               }
             }
             __syncthreads();
@@ -1831,25 +1934,28 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               }
             }
             update_rows2<S>(V, ld, j, ca, cb, E::coef(c.dcoef), scal_inv<S>(c), zp, Wv,
-                            zfinal ? nullptr : V + (size_t)j * ld, Z, !zfinal, lo, hi);
+                            zfinal ? nullptr : V + (size_t)j * ld, Z,
+                            zfinal ? PM_UPD_Q_IS_Z : single ? PM_UPD_SCALE : PM_UPD_REORTH, lo, hi);
             PM_MARK(7);
             PM_SYNC_OR_FAIL();                 // the next SpMV reads other CTAs' rows of the candidate
             PM_MARK(8);
             if (tid == 0) c.kcur = j;          // complete columns 0 .. j-1
           }
           if (!c.invariant) {
-            // complete the last candidate: v_target and column target-1
+            // complete the last candidate: v_target and column target-1 (its second
+            // projection only when the candidate needs one; otherwise just its norm)
             const int nq = target;
-            gs_vectors += nq;
-            dots_cta<S>(V, ld, nq, Z, lo, hi, true, s);
-            PM_BSUM_OR_FAIL(nq + 1);
-            for (int k = tid; k < nq; k += nth) s.h1[k] = s.coef[k];
+            const int na = c.skipz ? 0 : nq;   // basis vectors the completion pass reads
+            gs_vectors += na;
+            dots_cta<S>(V, ld, na, Z, lo, hi, true, s);
+            PM_BSUM_OR_FAIL(na + 1);
+            for (int k = tid; k < nq; k += nth) s.h1[k] = (k < na) ? s.coef[k] : 0.0;
             if (tid < 32) {
               double aa = 0.0;
-              for (int k = tid; k < nq; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
+              for (int k = tid; k < na; k += 32) aa = fma(s.coef[k], s.coef[k], aa);
               aa = pm_warp_sum(aa);
               if (tid == 0) {
-                c.fz = s.coef[nq];
+                c.fz = s.coef[na];
                 c.hn = c.fz - aa;
                 c.measure = (aa <= 0.25 * c.fz) ? 0 : 1;
               }
@@ -2219,6 +2325,7 @@ done:
     res.expms = c.expms;
     res.kry_steps = kry_steps;
     res.gs_vectors = gs_vectors;
+    res.reorth_vectors = reorth_vectors;
     res.err_est_sum = c.err_sum;
     res.normA = c.normA;
     res.normb = c.normb;

@@ -41,7 +41,7 @@ class OperatorC(ctypes.Structure):
 class StatsC(ctypes.Structure):
     _fields_ = [("steps", c_int64), ("rejects", c_int64), ("matvecs", c_int64), ("expms", c_int64),
                 ("err_est_sum", c_double), ("krylov_steps", c_int64), ("gs_vectors", c_int64),
-                ("kernel_ms", c_double)]
+                ("kernel_ms", c_double), ("reorth_vectors", c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
