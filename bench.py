@@ -407,6 +407,10 @@ def run_batched(args, world, rank, local):
     batch = solver.batch([pr.t_end for pr in probs], pk.ops, pk.bs, [pr.tol for pr in probs],
                          [pr.symm for pr in probs], outs=pk.outs)
 
+    tune = None
+    if not args.no_autotune:     # untimed: picks the cluster size K for this batch class
+        tune = batch.autotune(stream)
+
     def measure(controller):
         solver.set_controller(controller)
         for _ in range(args.warmup):
@@ -483,6 +487,8 @@ def run_batched(args, world, rank, local):
         outs_x = [torch.empty_like(x) for x in pk.outs]
         bx = sx.batch([pr.t_end for pr in probs], pk.ops, pk.bs, [tolx or pr.tol for pr in probs],
                       [pr.symm for pr in probs], outs=outs_x)
+        if not args.no_autotune:
+            bx.autotune(stream)
         for _ in range(args.warmup):
             bx.run(stream)
         torch.cuda.synchronize()
@@ -510,7 +516,7 @@ def run_batched(args, world, rank, local):
                    "n_total": int(sum(sizes)), "tol": probs[0].tol,
                    "l2": "flushed between timed batches (256 MiB write)",
                    "launch": "one persistent queue kernel per batch, replayed from a captured CUDA graph",
-                   "team": team,
+                   "team": team, "autotune_ms": {str(k): round(ms, 3) for k, ms in tune} if tune else None,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "solver_stats": {k: int(sum(x[k] for x in stats)) for k in ("steps", "rejects", "matvecs", "expms",
                                                                      "krylov_steps", "gs_vectors",

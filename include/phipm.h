@@ -317,19 +317,30 @@ typedef struct {
 phipm_status phipm_autotune(phipm_handle* h, double t_end, const phipm_operator* A, int32_t p,
                             const double* const* b, double tol, int32_t symm, double* u,
                             phipm_tune_entry* report, int32_t max_report, int32_t* n_report, void* stream);
+/* Batched counterpart: solves the batch (arguments as phipm_solve_batched) with
+ * each cluster size K = 1, 2, 4, 8 that the GPU can hold (K CTAs per problem; 1 =
+ * one CTA per problem), timing the second of two launches per K, and records the
+ * fastest for the batch class (precision, floor(log2 count), floor(log2 of the
+ * largest n)); later phipm_solve_batched calls of that class use it.  u holds the
+ * last launch's results.  report / n_report as for phipm_autotune (team = K). */
+phipm_status phipm_autotune_batched(phipm_handle* h, int32_t count, const double* t_end, const phipm_operator* A,
+                                    const int32_t* p, const double* const* const* b, const double* tol,
+                                    const int32_t* symm, double* const* u, phipm_tune_entry* report,
+                                    int32_t max_report, int32_t* n_report, void* stream);
 /* Force a team size for every later solve of this handle (0 = the tuned table or
  * the default; larger than the co-resident grid is clamped to it).  For
  * phipm_solve_batched the team is a thread-block cluster of up to 8 CTAs per
- * problem (1 = one CTA per problem); by default the batch picks 1, 2 or 4 from
- * the share of its largest problem in the total work. */
+ * problem (1 = one CTA per problem); without a forced or tuned K the batch picks
+ * 1, 2 or 4 from the share of its largest problem in the total work. */
 phipm_status phipm_set_team(phipm_handle* h, int32_t team);
 /* The team size a solve of this shape would use now (0 for invalid arguments). */
 int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n);
 /* CTAs per problem (the cluster size K; 1 = one CTA per problem) of the last
  * phipm_solve_batched call on this handle; 0 before the first. */
 int32_t phipm_batched_team(const phipm_handle* h);
-/* Save / load the tuned table as JSON: {"sms": S, "entries": [{"precision": P,
- * "kind": K, "log2n": L, "team": G, "ms": T}, ...]}.  Loading merges the entries
+/* Save / load the tuned tables as JSON: {"sms": S, "entries": [{"precision": P,
+ * "kind": K, "log2n": L, "team": G, "ms": T}, ...], "batch_entries": [{"precision": P,
+ * "log2count": C, "log2nmax": L, "team": K, "ms": T}, ...]}.  Loading merges the entries
  * into the handle's table when S equals this GPU's SM count and ignores the file
  * otherwise; a file that cannot be read or parsed returns PHIPM_EINVAL and
  * changes nothing. */

@@ -107,6 +107,10 @@ struct phipm_handle {
   std::map<int, std::pair<int, double>> tuned;
   int team_force = 0;
   int last_batch_team = 0;           // cluster size K of the last batched launch
+  // cluster size per batch class (precision, floor(log2 count), floor(log2 largest n)),
+  // from phipm_autotune_batched or a loaded cache; batch_req forces K while the tuner runs
+  std::map<int, std::pair<int, double>> tuned_batch;
+  int batch_req = 0;
 #ifdef PM_PHASE_PROBE
   DevBuf phase;                      // probe build: clock cycles per solver phase
 #endif
@@ -483,11 +487,13 @@ static bool any_csr(const DevProblem* probs, int count) {
 // ------------------------------------------------------------------------------------
 // single solve
 // ------------------------------------------------------------------------------------
-static int size_class(int prec, int kind, int n) {
+static int ilog2(long long n) {
   int lg = 0;
-  while (lg < 30 && (2ll << lg) <= (long long)n) ++lg;    // floor(log2 n)
-  return prec * 10000 + kind * 1000 + lg;
+  while (lg < 62 && (2ll << lg) <= n) ++lg;    // floor(log2 n), 0 for n <= 1
+  return lg;
 }
+static int size_class(int prec, int kind, int n) { return prec * 10000 + kind * 1000 + ilog2(n); }
+static int batch_class(int prec, int count, int nmax) { return prec * 10000 + ilog2(count) * 100 + ilog2(nmax); }
 
 // CTAs that cooperate on one problem: forced, tuned for the size class, or the default
 // (every SM from n = 16384 on, else one CTA).
@@ -738,14 +744,18 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
   const SlotLayout lay = slot_layout(nmax, pmax, h->params.m_max, es);
   // Team per problem: one CTA (queue) or a cluster of K CTAs.  phipm_set_team forces K
-  // (up to 8); otherwise K grows with the share of the largest problem in the batch's
-  // work: with ratio = SMs x largest cost / total cost, K = 1 below 0.5 (many similar
-  // problems keep every SM busy), 2 below 1, else 4 (measured on the 256-problem
-  // uneven batch: K = 1, 2, 4, 8 give 471, 805, 1140, 946 solves/s; on 1024 equal
-  // problems K = 1 is fastest).
+  // (up to 8); else the K that phipm_autotune_batched measured fastest for this batch
+  // class; else K grows with the share of the largest problem in the batch's work: with
+  // ratio = SMs x largest cost / total cost, K = 1 below 0.5 (many similar problems keep
+  // every SM busy), 2 below 1, else 4.
   int K;
-  if (h->team_force > 0) {
+  const auto tb = h->tuned_batch.find(batch_class(prec, count, nmax));
+  if (h->batch_req > 0) {
+    K = h->batch_req;
+  } else if (h->team_force > 0) {
     K = std::min(h->team_force, 8);
+  } else if (tb != h->tuned_batch.end()) {
+    K = tb->second.first;
   } else {
     double cmax = 0.0, csum = 0.0;
     for (int i = 0; i < count; ++i) {
@@ -1002,6 +1012,43 @@ extern "C" phipm_status phipm_autotune(phipm_handle* h, double t_end, const phip
   return PHIPM_OK;
 }
 
+extern "C" phipm_status phipm_autotune_batched(phipm_handle* h, int32_t count, const double* t_end,
+                                              const phipm_operator* A, const int32_t* p,
+                                              const double* const* const* b, const double* tol, const int32_t* symm,
+                                              double* const* u, phipm_tune_entry* report, int32_t max_report,
+                                              int32_t* n_report, void* stream) {
+  if (!h) return PHIPM_EINVAL;
+  if (n_report) *n_report = 0;
+  if (count <= 0 || !A) return fail(h, PHIPM_EINVAL, "autotune_batched needs count > 0");
+  const int prec = h->params.precision;
+  int nmax = 1;
+  for (int i = 0; i < count; ++i) nmax = std::max(nmax, op_n(&A[i]));
+  std::vector<phipm_stats> st((size_t)count);
+  int best = 0, k = 0;
+  double best_ms = 0.0;
+  for (int K : {1, 2, 4, 8}) {
+    if (K >= 2 && cluster_capacity(prec, K) < 1) continue;
+    h->batch_req = K;
+    double ms = 0.0;
+    phipm_status r = PHIPM_OK;
+    for (int rep = 0; rep < 2 && r == PHIPM_OK; ++rep) {   // the second run is timed (the first captures the graph)
+      r = phipm_solve_batched(h, count, t_end, A, p, b, tol, symm, u, st.data(), nullptr, stream);
+      ms = st[0].kernel_ms;
+    }
+    h->batch_req = 0;
+    if (r != PHIPM_OK) return r;
+    if (report && k < max_report) {
+      report[k].team = K;
+      report[k].kernel_ms = ms;
+    }
+    ++k;
+    if (best == 0 || ms < best_ms) { best = K; best_ms = ms; }
+  }
+  if (n_report) *n_report = std::min(k, max_report);
+  h->tuned_batch[batch_class(prec, count, nmax)] = {best, best_ms};
+  return PHIPM_OK;
+}
+
 extern "C" phipm_status phipm_set_team(phipm_handle* h, int32_t team) {
   if (!h) return PHIPM_EINVAL;
   if (team < 0) return fail(h, PHIPM_EINVAL, "team < 0");
@@ -1042,6 +1089,14 @@ extern "C" phipm_status phipm_tune_save(phipm_handle* h, const char* path) {
             key / 10000, (key / 1000) % 10, key % 1000, kv.second.first, kv.second.second);
     first = false;
   }
+  fprintf(f, "\n], \"batch_entries\": [");
+  first = true;
+  for (const auto& kv : h->tuned_batch) {
+    const int key = kv.first;
+    fprintf(f, "%s\n  {\"precision\": %d, \"log2count\": %d, \"log2nmax\": %d, \"team\": %d, \"ms\": %.6g}",
+            first ? "" : ",", key / 10000, (key / 100) % 100, key % 100, kv.second.first, kv.second.second);
+    first = false;
+  }
   fprintf(f, "\n]}\n");
   const bool ok = fclose(f) == 0;
   return ok ? PHIPM_OK : fail(h, PHIPM_EINVAL, std::string("cannot write ") + path);
@@ -1076,21 +1131,29 @@ extern "C" phipm_status phipm_tune_load(phipm_handle* h, const char* path) {
   if (lb == std::string::npos || !json_int(text.substr(0, lb), "sms", sms))
     return fail(h, PHIPM_EINVAL, "tuning cache: no sms / entries");
   if (sms != h->num_sms) return PHIPM_OK;     // tuned on another GPU: nothing applies
-  std::map<int, std::pair<int, double>> add;
+  std::map<int, std::pair<int, double>> add, add_batch;
   size_t pos = lb;
   while (true) {
     const size_t a = text.find('{', pos), z = (a == std::string::npos) ? a : text.find('}', a);
     if (a == std::string::npos || z == std::string::npos) break;
     const std::string obj = text.substr(a, z - a + 1);
-    long long pr, kd, lg, tm;
-    if (!json_int(obj, "precision", pr) || !json_int(obj, "kind", kd) || !json_int(obj, "log2n", lg) ||
-        !json_int(obj, "team", tm) || pr < 0 || pr > 2 || kd < 0 || kd > 1 || lg < 0 || lg > 30 || tm < 1 ||
-        tm > 1 << 20)
-      return fail(h, PHIPM_EINVAL, "tuning cache: malformed entry");
-    add[(int)(pr * 10000 + kd * 1000 + lg)] = {(int)tm, 0.0};
+    long long pr, kd, lg, tm, lc;
+    if (json_int(obj, "log2count", lc)) {     // a batched entry: cluster size K per batch class
+      if (!json_int(obj, "precision", pr) || !json_int(obj, "log2nmax", lg) || !json_int(obj, "team", tm) || pr < 0 ||
+          pr > 2 || lc < 0 || lc > 31 || lg < 0 || lg > 31 || (tm != 1 && tm != 2 && tm != 4 && tm != 8))
+        return fail(h, PHIPM_EINVAL, "tuning cache: malformed batch entry");
+      add_batch[(int)(pr * 10000 + lc * 100 + lg)] = {(int)tm, 0.0};
+    } else {
+      if (!json_int(obj, "precision", pr) || !json_int(obj, "kind", kd) || !json_int(obj, "log2n", lg) ||
+          !json_int(obj, "team", tm) || pr < 0 || pr > 2 || kd < 0 || kd > 1 || lg < 0 || lg > 30 || tm < 1 ||
+          tm > 1 << 20)
+        return fail(h, PHIPM_EINVAL, "tuning cache: malformed entry");
+      add[(int)(pr * 10000 + kd * 1000 + lg)] = {(int)tm, 0.0};
+    }
     pos = z + 1;
   }
   for (const auto& kv : add) h->tuned[kv.first] = kv.second;
+  for (const auto& kv : add_batch) h->tuned_batch[kv.first] = kv.second;
   return PHIPM_OK;
 }
 

@@ -744,22 +744,31 @@ __device__ __forceinline__ typename Elem<S>::Red dot_segment(const S* __restrict
   return E::red_of(acc0, acc1);
 }
 
+// One chunk of rows [lo, hi) of dots_cta (more than two products); y staged in shared
+// memory (the chunk fits), acc adds the chunk's sums to s.coef.
 template <class S>
-__device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo, int hi,
-                         bool with_norm, PmShared& s) {
+__device__ __forceinline__ void dots_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y,
+                                          int lo, int hi, bool with_norm, bool acc, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + (with_norm ? 1 : 0);
-  if (nvec <= 2) {           // one or two products: one pass over rows, y loaded once
-    dots_rows<S>(V, ld, nv, y, lo, hi, with_norm, s);
-    return;
-  }
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    if (!acc)
+      for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
+  }
+  {
+    constexpr int VEC = 16 / sizeof(S);
+    S* sy = reinterpret_cast<S*>(s.zw);
+    const int nq = (int)(rows / VEC);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x)
+      reinterpret_cast<float4*>(sy)[q] = *reinterpret_cast<const float4*>(y + lo + q * VEC);
+    for (int r = nq * VEC + threadIdx.x; r < rows; r += blockDim.x) sy[r] = y[lo + r];
+    __syncthreads();
+    y = sy - lo;                                  // indexed by absolute row, like V
   }
   // run length, a multiple of 4 rows.  A run meets at most run / rows + 2 vectors,
   // and run <= nvec rows / 16 + 4 rows with nvec <= 65 keeps that below 12 <= PM_DSEG.
@@ -783,9 +792,26 @@ __device__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S*
     typename E::Red t = E::red_zero();
     for (long long w = fa / run; w <= fb / run && w < PM_WARPS; ++w)
       t = E::red_add(t, red_get<typename E::Red>(&s.dred[w * PM_DSEG + (int)(i - (w * run) / rows)]));
-    s.coef[i] = E::red_val(t);
+    s.coef[i] = acc ? s.coef[i] + E::red_val(t) : E::red_val(t);
   }
   __syncthreads();
+}
+
+template <class S>
+__device__ __noinline__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo,
+                                      int hi, bool with_norm, PmShared& s) {
+  const int nvec = nv + (with_norm ? 1 : 0);
+  if (nvec <= 2) {           // one or two products: one pass over rows, y loaded once
+    dots_rows<S>(V, ld, nv, y, lo, hi, with_norm, s);
+    return;
+  }
+  // y staged in shared memory in chunks, so that L2 serves it once per pass
+  constexpr int CH = (PM_ZW_BYTES / (int)sizeof(S)) & ~63;
+  if (hi - lo <= CH) {
+    dots_part<S>(V, ld, nv, y, lo, hi, with_norm, false, s);
+    return;
+  }
+  for (int c0 = lo; c0 < hi; c0 += CH) dots_part<S>(V, ld, nv, y, c0, min(hi, c0 + CH), with_norm, c0 != lo, s);
 }
 
 // y[r] -= sum_{i<nv} h_i V[i][r] over this CTA's rows, four consecutive rows
@@ -952,15 +978,17 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
 }
 
 template <class S, bool WIDE>
-__device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                          const S* __restrict__ w, int lo, int hi, bool with_ww, PmShared& s) {
+__device__ __forceinline__ void dots2_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                           const S* __restrict__ w, int lo, int hi, bool with_ww, bool acc,
+                                           PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + 1 + (with_ww ? 1 : 0);
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
+    if (!acc)
+      for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
   }
@@ -1031,10 +1059,28 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
       tz = E::red_add(tz, red_get<typename E::Red>(&s.dred[sl]));
       tw = E::red_add(tw, red_get<typename E::Red>(&s.dred[sl + 1]));
     }
-    s.coef[i] = E::red_val(tz);
-    s.coef[nvec + i] = E::red_val(tw);
+    s.coef[i] = acc ? s.coef[i] + E::red_val(tz) : E::red_val(tz);
+    s.coef[nvec + i] = acc ? s.coef[nvec + i] + E::red_val(tw) : E::red_val(tw);
   }
   __syncthreads();
+}
+
+// Rows of z and w that fit the shared staging, a multiple of 64 (a CTA's rows start at
+// a multiple of 64, so chunks keep the passes' 16-byte alignment).
+template <class S> __device__ __forceinline__ constexpr int pm_zw_rows() { return (PM_ZW_BYTES / (2 * (int)sizeof(S))) & ~63; }
+
+// The pass over the CTA's rows in chunks whose z and w fit the staging: L2 then serves
+// every basis element once and z and w once per pass, instead of once per vector.  The
+// sums of the chunks are added in order (FP64), so the result is deterministic.
+template <class S, bool WIDE>
+__device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                       const S* __restrict__ w, int lo, int hi, bool with_ww, PmShared& s) {
+  constexpr int CH = pm_zw_rows<S>();
+  if (hi - lo <= CH) {
+    dots2_part<S, WIDE>(V, ld, nv, z, w, lo, hi, with_ww, false, s);
+    return;
+  }
+  for (int c0 = lo; c0 < hi; c0 += CH) dots2_part<S, WIDE>(V, ld, nv, z, w, c0, min(hi, c0 + CH), with_ww, c0 != lo, s);
 }
 
 // The pass of an Arnoldi step whose candidate z keeps its single projection (no second
@@ -1043,15 +1089,16 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
 // as the runs of dots_cta over the nv + 3 (left, right) pairs, z and w staged in shared
 // memory when they fit.
 template <class S>
-__device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
+__device__ __forceinline__ void dots_skip_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                               const S* __restrict__ w, int lo, int hi, bool acc, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + 3;
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    if (!acc)
+      for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
   }
@@ -1096,10 +1143,23 @@ __device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld
     typename E::Red t = E::red_zero();
     for (long long w2 = fa / run; w2 <= fb / run && w2 < PM_WARPS; ++w2)
       t = E::red_add(t, red_get<typename E::Red>(&s.dred[w2 * PM_DSEG + (int)(i - (w2 * run) / rows)]));
-    s.coef[i] = E::red_val(t);
+    s.coef[i] = acc ? s.coef[i] + E::red_val(t) : E::red_val(t);
   }
   __syncthreads();
 }
+
+template <class S>
+__device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
+  constexpr int CH = pm_zw_rows<S>();
+  if (hi - lo <= CH) {
+    dots_skip_part<S>(V, ld, nv, z, w, lo, hi, false, s);
+    return;
+  }
+  for (int c0 = lo; c0 < hi; c0 += CH) dots_skip_part<S>(V, ld, nv, z, w, c0, min(hi, c0 + CH), c0 != lo, s);
+}
+
+
 
 // Fused update of the lagged Gram-Schmidt step over this CTA's rows:
 //   q = (z - sum_{i<nv} a_i V_i) * inv                  (written to qout when qout != 0)

@@ -123,6 +123,11 @@ def lib(build_if_needed: bool = True):
                                  c_double, c_int32, c_void_p, ctypes.POINTER(TuneEntryC), c_int32,
                                  ctypes.POINTER(c_int32), c_void_p]
     L.phipm_autotune.restype = c_int32
+    L.phipm_autotune_batched.argtypes = [c_void_p, c_int32, ctypes.POINTER(c_double), ctypes.POINTER(OperatorC),
+                                         ctypes.POINTER(c_int32), ctypes.POINTER(ctypes.POINTER(c_void_p)),
+                                         ctypes.POINTER(c_double), ctypes.POINTER(c_int32), ctypes.POINTER(c_void_p),
+                                         ctypes.POINTER(TuneEntryC), c_int32, ctypes.POINTER(c_int32), c_void_p]
+    L.phipm_autotune_batched.restype = c_int32
     L.phipm_set_team.argtypes = [c_void_p, c_int32]
     L.phipm_set_team.restype = c_int32
     L.phipm_team_for.argtypes = [c_void_p, c_int32, c_int32, c_int32]
@@ -412,6 +417,16 @@ class Batch:
         self.U = (c_void_p * cnt)(*[u.data_ptr() for u in self.outs])
         self.ST = (StatsC * cnt)()
         self.PS = (c_int32 * cnt)()
+
+    def autotune(self, stream=None) -> list:
+        """phipm_autotune_batched on this batch: time each cluster size K and keep the
+        fastest for its batch class.  Returns [(K, kernel_ms), ...] in the order tried."""
+        rep = (TuneEntryC * 8)()
+        cnt = c_int32(0)
+        st = lib().phipm_autotune_batched(self.solver.h, self.count, self.T, self.A, self.P, self.B, self.TOL, self.SY,
+                                          self.U, rep, 8, ctypes.byref(cnt), _stream_ptr(stream))
+        self.solver._check(st)
+        return [(rep[i].team, rep[i].kernel_ms) for i in range(cnt.value)]
 
     def run(self, stream=None, check: bool = True) -> int:
         st = lib().phipm_solve_batched(self.solver.h, self.count, self.T, self.A, self.P, self.B, self.TOL, self.SY,

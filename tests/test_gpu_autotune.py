@@ -78,3 +78,33 @@ def test_tuning_cache_round_trip(case, tmp_path):
     with pytest.raises(pm.PhipmError):
         s3.tune_load(bad)
     assert s3.team_for(0, pr.n) == 1
+
+
+def test_batched_autotune_picks_a_measured_cluster_size(tmp_path):
+    """phipm_autotune_batched times K = 1, 2, 4, 8 CTAs per problem on the batch, keeps the
+    fastest for the batch class, every K's results match the oracle, later batches of the
+    class use it, and the table round-trips through the JSON cache."""
+    probs = wl.batched_convdiff_problems(count=10, side_lo=24, side_hi=80, seed0=6300)
+    s = pm.Phipm("f64pair")
+    ops = [pm.DeviceOperator(p_.op) for p_ in probs]
+    bs = [[torch.as_tensor(x).cuda() for x in p_.b] for p_ in probs]
+    batch = s.batch([p_.t_end for p_ in probs], ops, bs, [p_.tol for p_ in probs], [0] * len(probs))
+    rep = batch.autotune()
+    ks = [k for k, _ in rep]
+    assert ks[0] == 1 and set(ks) <= {1, 2, 4, 8} and len(ks) >= 2
+    best = min(rep, key=lambda e: e[1])[0]
+    batch.run()
+    assert s.last_batched_team() == best
+    for p_, u in zip(probs, batch.outs):
+        ref, _ = O.phipm(p_.t_end, p_.op, p_.b, p_.tol, 0)
+        assert _rel(u, ref) <= 1e-8
+    path = tmp_path / "tune.json"
+    s.tune_save(path)
+    doc = json.loads(path.read_text())
+    assert len(doc["batch_entries"]) == 1 and doc["batch_entries"][0]["team"] == best
+    assert doc["batch_entries"][0]["log2count"] == 3
+    s2 = pm.Phipm("f64pair")
+    s2.tune_load(path)
+    b2 = s2.batch([p_.t_end for p_ in probs], ops, bs, [p_.tol for p_ in probs], [0] * len(probs))
+    b2.run()
+    assert s2.last_batched_team() == best
