@@ -744,23 +744,22 @@ __device__ __forceinline__ typename Elem<S>::Red dot_segment(const S* __restrict
   return E::red_of(acc0, acc1);
 }
 
-// One chunk of rows [lo, hi) of dots_cta (more than two products); y staged in shared
-// memory (the chunk fits), acc adds the chunk's sums to s.coef.
+// The run-per-warp pass of dots_cta (more than two products); the CTA's rows of y are
+// staged in shared memory when they fit (every product reads them).
 template <class S>
 __device__ __forceinline__ void dots_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y,
-                                          int lo, int hi, bool with_norm, bool acc, PmShared& s) {
+                                          int lo, int hi, bool with_norm, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + (with_norm ? 1 : 0);
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    if (!acc)
-      for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
   }
-  {
+  if (rows * (long long)sizeof(S) <= (long long)PM_ZW_BYTES) {
     constexpr int VEC = 16 / sizeof(S);
     S* sy = reinterpret_cast<S*>(s.zw);
     const int nq = (int)(rows / VEC);
@@ -792,11 +791,14 @@ __device__ __forceinline__ void dots_part(const S* __restrict__ V, long long ld,
     typename E::Red t = E::red_zero();
     for (long long w = fa / run; w <= fb / run && w < PM_WARPS; ++w)
       t = E::red_add(t, red_get<typename E::Red>(&s.dred[w * PM_DSEG + (int)(i - (w * run) / rows)]));
-    s.coef[i] = acc ? s.coef[i] + E::red_val(t) : E::red_val(t);
+    s.coef[i] = E::red_val(t);
   }
   __syncthreads();
 }
 
+// Out of line, so that it does not add to the register pressure of the Arnoldi loop
+// (it serves the rarer passes: the completion of an extension's last candidate and the
+// candidate's third projection; the Lanczos steps call dots_rows directly).
 template <class S>
 __device__ __noinline__ void dots_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ y, int lo,
                                       int hi, bool with_norm, PmShared& s) {
@@ -805,13 +807,7 @@ __device__ __noinline__ void dots_cta(const S* __restrict__ V, long long ld, int
     dots_rows<S>(V, ld, nv, y, lo, hi, with_norm, s);
     return;
   }
-  // y staged in shared memory in chunks, so that L2 serves it once per pass
-  constexpr int CH = (PM_ZW_BYTES / (int)sizeof(S)) & ~63;
-  if (hi - lo <= CH) {
-    dots_part<S>(V, ld, nv, y, lo, hi, with_norm, false, s);
-    return;
-  }
-  for (int c0 = lo; c0 < hi; c0 += CH) dots_part<S>(V, ld, nv, y, c0, min(hi, c0 + CH), with_norm, c0 != lo, s);
+  dots_part<S>(V, ld, nv, y, lo, hi, with_norm, s);
 }
 
 // y[r] -= sum_{i<nv} h_i V[i][r] over this CTA's rows, four consecutive rows
@@ -954,6 +950,24 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
     }
   }
   e += 4 * lane;
+  if constexpr (sizeof(S) == 4) {
+    // FP32 basis: four quads of V per lane in flight (64 bytes; 32 KB per SM), enough
+    // bytes in flight to stream the basis from HBM at full bandwidth
+    for (; e + 384 + 3 < qb; e += 512) {
+      Quad<S> vq[4], zq[4], wq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) vq[u].load(v + e + 128 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { zq[u].load(z + e + 128 * u); wq[u].load(w + e + 128 * u); }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          E::dot((u & 1) ? z1 : z0, vq[u].x[k], zq[u].x[k]);
+          E::dot((u & 1) ? w1 : w0, vq[u].x[k], wq[u].x[k]);
+        }
+    }
+  }
   for (; e + 128 + 3 < qb; e += 256) {        // two quads of each operand per lane in flight
     Quad<S> v0, v1, z0q, z1q, w0q, w1q;
     v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
@@ -978,17 +992,15 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
 }
 
 template <class S, bool WIDE>
-__device__ __forceinline__ void dots2_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                                           const S* __restrict__ w, int lo, int hi, bool with_ww, bool acc,
-                                           PmShared& s) {
+__device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                       const S* __restrict__ w, int lo, int hi, bool with_ww, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + 1 + (with_ww ? 1 : 0);
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    if (!acc)
-      for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
+    for (int i = threadIdx.x; i < 2 * nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
   }
@@ -1059,28 +1071,10 @@ __device__ __forceinline__ void dots2_part(const S* __restrict__ V, long long ld
       tz = E::red_add(tz, red_get<typename E::Red>(&s.dred[sl]));
       tw = E::red_add(tw, red_get<typename E::Red>(&s.dred[sl + 1]));
     }
-    s.coef[i] = acc ? s.coef[i] + E::red_val(tz) : E::red_val(tz);
-    s.coef[nvec + i] = acc ? s.coef[nvec + i] + E::red_val(tw) : E::red_val(tw);
+    s.coef[i] = E::red_val(tz);
+    s.coef[nvec + i] = E::red_val(tw);
   }
   __syncthreads();
-}
-
-// Rows of z and w that fit the shared staging, a multiple of 64 (a CTA's rows start at
-// a multiple of 64, so chunks keep the passes' 16-byte alignment).
-template <class S> __device__ __forceinline__ constexpr int pm_zw_rows() { return (PM_ZW_BYTES / (2 * (int)sizeof(S))) & ~63; }
-
-// The pass over the CTA's rows in chunks whose z and w fit the staging: L2 then serves
-// every basis element once and z and w once per pass, instead of once per vector.  The
-// sums of the chunks are added in order (FP64), so the result is deterministic.
-template <class S, bool WIDE>
-__device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                                       const S* __restrict__ w, int lo, int hi, bool with_ww, PmShared& s) {
-  constexpr int CH = pm_zw_rows<S>();
-  if (hi - lo <= CH) {
-    dots2_part<S, WIDE>(V, ld, nv, z, w, lo, hi, with_ww, false, s);
-    return;
-  }
-  for (int c0 = lo; c0 < hi; c0 += CH) dots2_part<S, WIDE>(V, ld, nv, z, w, c0, min(hi, c0 + CH), with_ww, c0 != lo, s);
 }
 
 // The pass of an Arnoldi step whose candidate z keeps its single projection (no second
@@ -1089,16 +1083,15 @@ __device__ __noinline__ void dots2_cta(const S* __restrict__ V, long long ld, in
 // as the runs of dots_cta over the nv + 3 (left, right) pairs, z and w staged in shared
 // memory when they fit.
 template <class S>
-__device__ __forceinline__ void dots_skip_part(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                                               const S* __restrict__ w, int lo, int hi, bool acc, PmShared& s) {
+__device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
+                                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
   typedef Elem<S> E;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long rows = hi - lo;
   const int nvec = nv + 3;
   const long long total = (long long)nvec * rows;
   if (total == 0) {
-    if (!acc)
-      for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) s.coef[i] = 0.0;
     __syncthreads();
     return;
   }
@@ -1143,23 +1136,10 @@ __device__ __forceinline__ void dots_skip_part(const S* __restrict__ V, long lon
     typename E::Red t = E::red_zero();
     for (long long w2 = fa / run; w2 <= fb / run && w2 < PM_WARPS; ++w2)
       t = E::red_add(t, red_get<typename E::Red>(&s.dred[w2 * PM_DSEG + (int)(i - (w2 * run) / rows)]));
-    s.coef[i] = acc ? s.coef[i] + E::red_val(t) : E::red_val(t);
+    s.coef[i] = E::red_val(t);
   }
   __syncthreads();
 }
-
-template <class S>
-__device__ __noinline__ void dots_skip_cta(const S* __restrict__ V, long long ld, int nv, const S* __restrict__ z,
-                                           const S* __restrict__ w, int lo, int hi, PmShared& s) {
-  constexpr int CH = pm_zw_rows<S>();
-  if (hi - lo <= CH) {
-    dots_skip_part<S>(V, ld, nv, z, w, lo, hi, false, s);
-    return;
-  }
-  for (int c0 = lo; c0 < hi; c0 += CH) dots_skip_part<S>(V, ld, nv, z, w, c0, min(hi, c0 + CH), c0 != lo, s);
-}
-
-
 
 // Fused update of the lagged Gram-Schmidt step over this CTA's rows:
 //   q = (z - sum_{i<nv} a_i V_i) * inv                  (written to qout when qout != 0)
@@ -2084,7 +2064,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
             __syncthreads();
             {
               // Algorithm 2: t_jj = v_j^T y ; y <- y - t_{j,j-1} v_{j-1} - t_jj v_j ; t_{j+1,j} = ||y||
-              dots_cta<S>(V + (size_t)j * ld, ld, 1, ycur, lo, hi, false, s);
+              dots_rows<S>(V + (size_t)j * ld, ld, 1, ycur, lo, hi, false, s);
               PM_BSUM_OR_FAIL(1);
               if (tid == 0) {
                 const double tjj = s.coef[0];
@@ -2096,7 +2076,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               if (j > 0) update_rows<S>(ycur, V + (size_t)(j - 1) * ld, ld, 2, hc, lo, hi);
               else update_rows<S>(ycur, V, ld, 1, hc, lo, hi);
               __syncthreads();
-              dots_cta<S>(ycur, ld, 0, ycur, lo, hi, true, s);
+              dots_rows<S>(ycur, ld, 0, ycur, lo, hi, true, s);
               PM_BSUM_OR_FAIL(1);
               if (tid == 0) {
                 const double hn = sqrt(s.coef[0]);
