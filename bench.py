@@ -397,7 +397,8 @@ def run_batched(args, world, rank, local):
         from paper_0907_4631_gb300 import learned as L
         t0 = time.perf_counter()
         tr = L.training_problems(count=768, seed0=7000)
-        X, T = L.examples_from_traces(L.collect_traces(solver, tr))
+        traces = L.collect_traces(solver, tr)
+        X, T = L.examples_from_traces(traces)
         blob, losses = L.train(solver, X, T, iters=3000, lr=3e-3)
         solver.set_controller_weights(blob)
         learned = {"training_problems": len(tr), "examples": int(X.shape[0]), "adam_iters": 3000,
@@ -418,13 +419,26 @@ def run_batched(args, world, rank, local):
         torch.cuda.synchronize()
         return time_batch(batch, stream, flush, args.steps), batch.stats()
 
-    plain = None
+    plain = every = None
     if learned is not None:
+        # the learned controller that proposes every step, with its own network (reported;
+        # the headline keeps the first-step proposal, measured faster)
+        X3, T3 = L.examples_every_step(traces)
+        blob3, losses3 = L.train(solver, X3, T3, iters=3000, lr=3e-3)
+        solver.set_controller_weights(blob3)
+        et_, est = measure(3)
+        every = {"value": world * count * args.steps / (sum(et_) / 1e3), "unit": "solves/s",
+                 "examples": int(X3.shape[0]), "loss_last": float(losses3[-1]),
+                 "rejects": int(sum(x["rejects"] for x in est)), "steps": int(sum(x["steps"] for x in est)),
+                 "matvecs": int(sum(x["matvecs"] for x in est)),
+                 "gs_vectors": int(sum(x["gs_vectors"] for x in est))}
+        solver.set_controller_weights(blob)
         pt, pst = measure(0)
         plain = {"value": world * count * args.steps / (sum(pt) / 1e3), "unit": "solves/s",
                  "rejects": int(sum(x["rejects"] for x in pst)), "steps": int(sum(x["steps"] for x in pst)),
                  "matvecs": int(sum(x["matvecs"] for x in pst)),
-                 "krylov_steps": int(sum(x["krylov_steps"] for x in pst))}
+                 "krylov_steps": int(sum(x["krylov_steps"] for x in pst)),
+                 "gs_vectors": int(sum(x["gs_vectors"] for x in pst))}
         u_plain = [u.cpu().numpy() for u in pk.outs]
     sampler = ClockSampler(local)
     for _ in range(args.warmup):
@@ -531,6 +545,9 @@ def run_batched(args, world, rank, local):
     if learned is not None:
         line["learned"] = learned
         line["plain_controller"] = plain
+        line["learned_every_step_controller"] = every
+        line["learned_first_step_counters"] = {k: int(sum(x[k] for x in stats))
+                                               for k in ("rejects", "steps", "matvecs", "gs_vectors")}
         line["plain_vs_learned_max_rel_diff"] = float(max(
             np.linalg.norm(a - b_) / np.linalg.norm(b_) for a, b_ in zip(u_gpu, u_plain)))
     if e2e:

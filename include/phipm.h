@@ -131,8 +131,8 @@ typedef struct {
   int64_t max_steps;
   int64_t max_rejects;
   int32_t precision;      /* phipm_precision */
-  int32_t controller;     /* phipm_controller: 0 = the paper's controller; 1 = learned
-                             proposal (see below); 2 = fixed Krylov dimension (phip) */
+  int32_t controller;     /* phipm_controller: 0 = the paper's controller; 1, 3 = learned
+                             proposals (see below); 2 = fixed Krylov dimension (phip) */
   int64_t timeout_cycles; /* bound on every device-side spin-wait, in clock64 cycles */
 } phipm_params;
 
@@ -141,7 +141,12 @@ typedef struct {
  * Algorithm 3 never taken, so every attempt uses m = m_init (shortened only by a
  * happy breakdown, as in phipm) and only tau adapts (Eq. taunew with the q
  * estimate of Eq. 6). */
-typedef enum { PHIPM_CTRL_PAPER = 0, PHIPM_CTRL_LEARNED = 1, PHIPM_CTRL_FIXED_M = 2 } phipm_controller;
+typedef enum {
+  PHIPM_CTRL_PAPER = 0,
+  PHIPM_CTRL_LEARNED = 1,        /* the network proposes the first attempt of the first step */
+  PHIPM_CTRL_FIXED_M = 2,
+  PHIPM_CTRL_LEARNED_STEPS = 3   /* the network proposes the first attempt of every step     */
+} phipm_controller;
 
 #define PHIPM_M_MAX 64
 #define PHIPM_P_MAX 8
@@ -235,11 +240,14 @@ phipm_status phipm_trace_read(phipm_handle* h, phipm_trace_record* out, int64_t 
  *   attempts in the previous step, log10(n),
  * where tau_start, m_start are the values Algorithm 3 carries into the step.
  * Outputs: log2(tau / tau_start) and m / 64 of the proposal.  With
- * params.controller = 1 and a blob installed, the first attempt of the first
- * step uses the proposal in place of Eq. (tau_0) and m_init (tau ratio clamped
- * to [1/32, 8] and to the interval, m to [1, m_max]); the error estimate still
- * accepts or rejects it, and the paper's controller handles every later attempt
- * and step, whose proposals already rest on a measured error estimate. */
+ * params.controller = PHIPM_CTRL_LEARNED and a blob installed, the first attempt
+ * of the first step uses the proposal in place of Eq. (tau_0) and m_init (tau
+ * ratio clamped to [1/32, 8] and to the interval, m to [1, m_max]); the error
+ * estimate still accepts or rejects it, and the paper's controller handles every
+ * later attempt and step.  With PHIPM_CTRL_LEARNED_STEPS the first attempt of
+ * every step uses a proposal from the live state (same clamps); after a rejected
+ * attempt the paper's controller takes over for the rest of the step.  The two
+ * modes want networks trained on different labels (learned.py). */
 #define PHIPM_MLP_PARAMS 4866
 #define PHIPM_CONTROLLER_FLOATS (PHIPM_MLP_PARAMS + 20)
 phipm_status phipm_set_controller_weights(phipm_handle* h, const float* blob, size_t count);

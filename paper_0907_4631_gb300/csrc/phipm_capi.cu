@@ -149,7 +149,7 @@ static bool params_ok(const phipm_params& p, std::string& why) {
     why = "unknown precision";
     return false;
   }
-  if (p.controller < 0 || p.controller > 2) { why = "unknown controller"; return false; }
+  if (p.controller < 0 || p.controller > 3) { why = "unknown controller"; return false; }
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
   return true;
 }
@@ -264,6 +264,7 @@ static DevParams make_params(const phipm_params& p) {
   d.m_init = p.m_init;
   d.m_max = p.m_max;
   d.fixed_m = (p.controller == PHIPM_CTRL_FIXED_M) ? 1 : 0;
+  d.mlp_every_step = (p.controller == PHIPM_CTRL_LEARNED_STEPS) ? 1 : 0;
   d.max_steps = p.max_steps;
   d.max_rejects = p.max_rejects;
   d.timeout_cycles = p.timeout_cycles;
@@ -431,8 +432,8 @@ static phipm_status attach_runtime(phipm_handle* h, DevParams& prm, cudaStream_t
   }
   prm.phase_ticks = (unsigned long long*)h->phase.p;
 #endif
-  if (h->params.controller == 1) {
-    if (!h->has_mlp) return fail(h, PHIPM_EINVAL, "controller = 1 needs phipm_set_controller_weights");
+  if (h->params.controller == PHIPM_CTRL_LEARNED || h->params.controller == PHIPM_CTRL_LEARNED_STEPS) {
+    if (!h->has_mlp) return fail(h, PHIPM_EINVAL, "a learned controller needs phipm_set_controller_weights");
     prm.mlp = (const float*)h->mlp_blob.p;
   }
   if (h->trace_cap > 0) {

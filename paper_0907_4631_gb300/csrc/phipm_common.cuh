@@ -58,7 +58,7 @@ struct DevParams {
   double gamma, delta, theta13, breakdown_tol;
   int m_init, m_max;
   int fixed_m;           // 1: the m branch of Algorithm 3 is never taken (phip)
-  int pad0;
+  int mlp_every_step;    // 1: the learned controller proposes the first attempt of every step
   long long max_steps, max_rejects;
   long long timeout_cycles;
   double pade_b[14];     // degree-13 Pade coefficients, computed on the host from their closed form

@@ -1763,11 +1763,12 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       ctl_reset(ctl);
     }
     __syncthreads();
-    if (prm.mlp != nullptr && c.steps == 0 && tid < 32) {
+    if (prm.mlp != nullptr && (c.steps == 0 || prm.mlp_every_step) && tid < 32) {
       // learned controller (a11): propose (tau, m) for the first attempt of the first
-      // step, in place of Eq. (tau_0) and m_init.  Later steps start from proposals of
-      // Algorithm 4 that rest on a measured error estimate; applied there too, small
-      // biases of the network compound from step to step (tau shrinking geometrically).
+      // step, in place of Eq. (tau_0) and m_init, or (mlp_every_step) for the first
+      // attempt of every step, from the live state: the tau and m Algorithm 4 carried
+      // into the step, omega of the last accepted attempt and the last step's rejects.
+      // After a rejected attempt Algorithm 4 takes over for the rest of the step.
       const float* blob = prm.mlp;
       if (tid == 0) {
         const double raw[MLP_IN] = {log10(c.normA * c.t_end), log10(c.tol), (double)p, log10(c.tau * c.normA),
@@ -1787,9 +1788,22 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
           const double lr = (double)y[0] * blob[MLP_NP + 2 * MLP_IN + 2] + blob[MLP_NP + 2 * MLP_IN];
           const double mm = (double)y[1] * blob[MLP_NP + 2 * MLP_IN + 3] + blob[MLP_NP + 2 * MLP_IN + 1];
           if (isfinite(lr) && isfinite(mm)) {
-            const double ratio = exp2(fmin(fmax(lr, -5.0), 3.0));
-            c.tau = fmin(c.tau * ratio, c.t_end - c.t);
-            c.m = (int)fmin(fmax(rint(64.0 * mm), 1.0), (double)prm.m_max);
+            if (c.steps == 0) {
+              // the first step: Eq. (tau_0) and m_init are guesses, so the proposal may move
+              // tau by 1/32 .. 8 and m anywhere in [1, m_max]
+              const double ratio = exp2(fmin(fmax(lr, -5.0), 3.0));
+              c.tau = fmin(c.tau * ratio, c.t_end - c.t);
+              c.m = (int)fmin(fmax(rint(64.0 * mm), 1.0), (double)prm.m_max);
+            } else {
+              // later steps start from Algorithm 4's measured proposal: the network only
+              // corrects it within tau / 2 .. 2 tau and Algorithm 3's m range [3m/4, 4m/3],
+              // so a biased proposal cannot compound from step to step
+              const double ratio = exp2(fmin(fmax(lr, -1.0), 1.0));
+              c.tau = fmin(c.tau * ratio, c.t_end - c.t);
+              const int m0 = c.m;
+              const int mp = (int)rint(64.0 * mm);
+              c.m = min(min(max(max(mp, (3 * m0) / 4), 1), (4 * m0 + 2) / 3), prm.m_max);
+            }
             c.source = 1;
           }
         }

@@ -16,13 +16,14 @@ this module builds arrays and calls the library):
        - first step accepted at once: the (tau, m) the paper's controller
          proposes right after it (its estimate from a measured error), unless
          that proposal was cut to the end of the interval;
-     The proposal is not applied to later steps: their start values already
-     rest on a measured error estimate, and small biases of a network
-     applied at every step compound (tau shrinking geometrically);
+     For the controller that proposes every step (examples_every_step) each
+     step gives an example, labelled with the largest tau its own accepted
+     attempt supports (Eq. 2 with the margin gamma);
   3. standardise, train the 8-64-64-2 GELU network with phipm_mlp_train
      (full-batch Adam, mean squared error);
   4. install the blob (weights + standardisation) with
-     phipm_set_controller_weights and solve with params.controller = 1.
+     phipm_set_controller_weights and solve with params.controller = 1 (first
+     step) or 3 (every step).
 
 The feature definition must match the solver's (csrc/phipm_engine.cuh, learned
 proposal block):
@@ -122,6 +123,58 @@ def examples_from_traces(records: list) -> tuple:
         if all(math.isfinite(v) for v in x + t):
             X.append(x)
             T.append(t)
+    return np.asarray(X, dtype=np.float64).reshape(-1, N_FEATURES), np.asarray(T, dtype=np.float64).reshape(-1, 2)
+
+
+def _q_estimate(attempts: list) -> float:
+    """q of Eq. (6) from two attempts of a step at the same m and different tau (the
+    error model eps ~ tau^(q+1)), else m / 4 as Algorithm 4 starts; clamped to [0, m]."""
+    acc = attempts[-1]
+    m = acc["m_used"]
+    for r in reversed(attempts[:-1]):
+        if r["m_used"] == m and r["tau"] != acc["tau"] and r["eps"] > 0 and acc["eps"] > 0:
+            q = math.log(acc["eps"] / r["eps"]) / math.log(acc["tau"] / r["tau"]) - 1.0
+            if math.isfinite(q):
+                return min(max(q, 0.0), float(m))
+    return m / 4.0
+
+
+def examples_every_step(records: list, gamma: float = 0.8) -> tuple:
+    """(X_raw, T_raw) for the controller that proposes the first attempt of every step
+    (PHIPM_CTRL_LEARNED_STEPS): one example per step, features at the step's start
+    (the tau and m Algorithm 4 carried into it, omega of the previous accepted attempt,
+    the previous step's rejects) and as label the largest tau the step's own accepted
+    attempt supports with the margin gamma of Eq. (2), tau* = tau_acc (gamma /
+    omega_acc)^(1/(q+1)) with q from the step's attempts (Eq. 6) or m / 4, together
+    with the accepted m.  Unlike the accepted tau, tau* is not biased below what the
+    step could take, so the proposals do not shrink from step to step.  Steps cut to
+    the end of the interval and steps with a zero estimate give no example."""
+    by_prob: dict = {}
+    for r in records:
+        by_prob.setdefault(r["problem"], {}).setdefault(r["step"], []).append(r)
+    X, T = [], []
+    for prob, steps in by_prob.items():
+        omega_prev = 1.0
+        for k in sorted(steps):
+            att = sorted(steps[k], key=lambda r: r["attempt"])
+            acc = [r for r in att if r["accepted"]]
+            if not acc or att[0]["attempt"] != 0:
+                break
+            r0, ra = att[0], acc[-1]
+            upto = att[:att.index(ra) + 1]
+            last = ra["t"] + ra["tau"] >= ra["t_end"] * (1.0 - 1e-12)
+            na = r0["norm_a"]
+            if not last and ra["omega"] > 0 and na > 0 and r0["tau"] > 0:
+                q = _q_estimate(upto)
+                tau_star = ra["tau"] * (gamma / ra["omega"]) ** (1.0 / (q + 1.0))
+                x = [math.log10(na * r0["t_end"]), math.log10(r0["tol"]), float(r0["p"]),
+                     math.log10(r0["tau"] * na), r0["m_req"] / 64.0, math.log10(max(omega_prev, 1e-6)),
+                     float(r0["rejects_prev"]), math.log10(r0["n"])]
+                t = [math.log2(tau_star / r0["tau"]), ra["m_used"] / 64.0]
+                if all(math.isfinite(v) for v in x + t):
+                    X.append(x)
+                    T.append(t)
+            omega_prev = ra["omega"]
     return np.asarray(X, dtype=np.float64).reshape(-1, N_FEATURES), np.asarray(T, dtype=np.float64).reshape(-1, 2)
 
 

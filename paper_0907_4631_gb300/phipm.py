@@ -20,7 +20,7 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE, ENOTRUN = range(10)
 F64, F32_MIXED, F64_PAIR = 0, 1, 2
 OP_CSR, OP_STENCIL = 0, 1
-CTRL_PAPER, CTRL_LEARNED, CTRL_FIXED_M = 0, 1, 2      # phipm_controller
+CTRL_PAPER, CTRL_LEARNED, CTRL_FIXED_M, CTRL_LEARNED_STEPS = 0, 1, 2, 3      # phipm_controller
 M_MAX, P_MAX, NOALLOC_MAX_N = 64, 8, 8192
 MLP_PARAMS, CONTROLLER_FLOATS = 4866, 4886
 

@@ -71,7 +71,7 @@ def test_invalid_params_rejected_without_gpu():
     assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
     assert not h.value
     p = pm.default_params()
-    p.controller = pm.CTRL_FIXED_M + 1
+    p.controller = pm.CTRL_LEARNED_STEPS + 1
     assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
     assert not h.value
 
