@@ -66,7 +66,7 @@ typedef enum {
  * their products must stay inside the float range (about 3e38); in practice ||A|| up
  * to about 1e12.  The norms of u and w_p are always summed in FP64. */
 
-typedef enum { PHIPM_OP_CSR = 0, PHIPM_OP_STENCIL = 1 } phipm_op_kind;
+typedef enum { PHIPM_OP_CSR = 0, PHIPM_OP_STENCIL = 1, PHIPM_OP_FUNCTION = 2 } phipm_op_kind;
 
 /* CSR matrix, n x n.  rowptr[n+1], colind[nnz] (0-based, int32), values[nnz] (FP64).
  * For phipm_solve*: device pointers.  For phipm_solve_host: host pointers. */
@@ -89,10 +89,39 @@ typedef struct {
   double c_plus[3];
 } phipm_stencil;
 
+/* Matrix-free operator (Sec. 3.5: A may be given as a function that computes A x).
+ * A persistent GPU kernel can only apply device code of its own module, so the
+ * functions are built into the library and selected by id; the caller passes their
+ * data (device arrays and scalars) and, as with a function handle, may pass an upper
+ * bound of ||A||_inf (Eq. tau_0 and the breakdown threshold) and the cost N_A of one
+ * product (Eq. 4).  Symmetry is not detected: symm = -1 treats A as nonsymmetric
+ * (Arnoldi); pass symm = 1 for a symmetric function.
+ *
+ * PHIPM_FN_VARCOEF_CONVDIFF, variable-coefficient convection-diffusion on the
+ * nx x ny x nz grid of interior unknowns (i = x + nx (y + ny z), Dirichlet 0), with
+ * the diffusivity kappa = field[0] (n values > 0) and velocities v_d = field[1 + d]
+ * (n values, NULL = 0):
+ *   (A x)_i = sum_{d<ndim} ( s_d [ kp (x_{i+e_d} - x_i) - km (x_i - x_{i-e_d}) ]
+ *                            - c_d v_{d,i} (x_{i+e_d} - x_{i-e_d}) ),
+ * kp = (kappa_i + kappa_{i+e_d}) / 2 and km = (kappa_i + kappa_{i-e_d}) / 2 (kappa_i
+ * alone where the neighbour lies outside the grid, where x is 0), s_d = scal[d]
+ * (1 / h_d^2) and c_d = scal[3 + d] (1 / (2 h_d)).  Symmetric when every v_d is NULL. */
+typedef enum { PHIPM_FN_VARCOEF_CONVDIFF = 0 } phipm_fn_id;
+typedef struct {
+  int32_t fn;                 /* phipm_fn_id                                            */
+  int32_t ndim, nx, ny, nz;   /* grid (unused extents 1)                                */
+  int32_t reserved;
+  const double* field[4];     /* device arrays of n values; meaning per function        */
+  double scal[6];             /* scalars of the function                                */
+  double norm_inf;            /* an upper bound of ||A||_inf; <= 0: computed on the device */
+  int64_t cost;               /* N_A of Eq. (4); <= 0: the grid operator's structural nonzeros */
+} phipm_function;
+
 typedef struct {
   int32_t kind;           /* phipm_op_kind */
-  phipm_csr csr;          /* used when kind == PHIPM_OP_CSR     */
-  phipm_stencil st;       /* used when kind == PHIPM_OP_STENCIL */
+  phipm_csr csr;          /* used when kind == PHIPM_OP_CSR      */
+  phipm_stencil st;       /* used when kind == PHIPM_OP_STENCIL  */
+  phipm_function fn;      /* used when kind == PHIPM_OP_FUNCTION */
 } phipm_operator;
 
 /* stats(1..4) of Sec. 3.5 plus the sum of accepted error estimates.
@@ -177,7 +206,8 @@ phipm_status phipm_solve(phipm_handle* h, double t_end, const phipm_operator* A,
                          phipm_stats* stats, void* stream);
 
 /* Same computation with every array in host memory (CSR arrays, b[k], u):
- * copies the operator and b to the device, solves, and copies u back. */
+ * copies the operator and b to the device, solves, and copies u back.  CSR and
+ * stencil operators only (PHIPM_EINVAL for a function operator). */
 phipm_status phipm_solve_host(phipm_handle* h, double t_end, const phipm_operator* A_host,
                               int32_t p, const double* const* b_host, double tol, int32_t symm,
                               double* u_host, phipm_stats* stats, void* stream);

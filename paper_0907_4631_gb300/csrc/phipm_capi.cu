@@ -305,11 +305,34 @@ static phipm_status check_operator(phipm_handle* h, const phipm_operator* A, lon
     for (int d = 0; d < st.ndim; ++d) nnz_model += 2 * (n / dims[d]) * (dims[d] - 1);
     return PHIPM_OK;
   }
+  if (A->kind == PHIPM_OP_FUNCTION) {
+    const phipm_function& f = A->fn;
+    if (f.fn != PHIPM_FN_VARCOEF_CONVDIFF) return fail(h, PHIPM_EINVAL, "unknown built-in function");
+    if (f.ndim < 1 || f.ndim > 3) return fail(h, PHIPM_EINVAL, "function ndim must be 1, 2 or 3");
+    if (f.nx < 1 || f.ny < 1 || f.nz < 1) return fail(h, PHIPM_EINVAL, "function grid extents must be >= 1");
+    if ((f.ndim < 2 && f.ny != 1) || (f.ndim < 3 && f.nz != 1)) return fail(h, PHIPM_EINVAL, "unused extents must be 1");
+    const long long n = (long long)f.nx * f.ny * f.nz;
+    if (n > 0x7fffffffll) return fail(h, PHIPM_EINVAL, "function grid too large for int32 indexing");
+    if (!f.field[0]) return fail(h, PHIPM_EINVAL, "the diffusivity field is NULL");
+    for (int d = 0; d < 6; ++d)
+      if (!std::isfinite(f.scal[d])) return fail(h, PHIPM_EINVAL, "function scalars must be finite");
+    if (!std::isfinite(f.norm_inf)) return fail(h, PHIPM_EINVAL, "norm_inf must be finite");
+    if (f.cost > 0) {
+      nnz_model = f.cost;
+    } else {
+      const long long dims[3] = {f.nx, f.ny, f.nz};
+      nnz_model = n;
+      for (int d = 0; d < f.ndim; ++d) nnz_model += 2 * (n / dims[d]) * (dims[d] - 1);
+    }
+    return PHIPM_OK;
+  }
   return fail(h, PHIPM_EINVAL, "unknown operator kind");
 }
 
 static int op_n(const phipm_operator* A) {
-  return A->kind == PHIPM_OP_CSR ? A->csr.n : A->st.nx * A->st.ny * A->st.nz;
+  if (A->kind == PHIPM_OP_CSR) return A->csr.n;
+  if (A->kind == PHIPM_OP_FUNCTION) return A->fn.nx * A->fn.ny * A->fn.nz;
+  return A->st.nx * A->st.ny * A->st.nz;
 }
 
 static df32 host_split(double c) {   // c = hi + lo with hi = fl32(c)
@@ -322,10 +345,22 @@ static df32 host_split(double c) {   // c = hi + lo with hi = fl32(c)
 static DevOp make_devop(const phipm_operator* A, long long nnz_model) {
   DevOp o;
   memset(&o, 0, sizeof(o));
-  o.kind = A->kind == PHIPM_OP_CSR ? 0 : 1;
+  o.kind = A->kind == PHIPM_OP_CSR ? 0 : A->kind == PHIPM_OP_FUNCTION ? 2 : 1;
   o.n = op_n(A);
   o.nnz = nnz_model;
-  if (o.kind == 0) {
+  if (o.kind == 2) {
+    const phipm_function& f = A->fn;
+    o.fn = f.fn;
+    o.ndim = f.ndim;
+    o.nx = f.nx;
+    o.ny = f.ny;
+    o.nz = f.nz;
+    for (int d = 0; d < 4; ++d) o.fld[d] = f.field[d];
+    for (int d = 0; d < 6; ++d) o.fsc[d] = f.scal[d];
+    o.fnorm = f.norm_inf;
+    o.mnx = o.nx >= 2 ? (~0ull / (unsigned long long)o.nx) + 1 : 0;
+    o.mny = o.ny >= 2 ? (~0ull / (unsigned long long)o.ny) + 1 : 0;
+  } else if (o.kind == 0) {
     o.rowptr = A->csr.rowptr;
     o.colind = A->csr.colind;
     o.val = A->csr.values;
@@ -656,6 +691,7 @@ extern "C" phipm_status phipm_solve_host(phipm_handle* h, double t_end, const ph
   long long nnz_model = 0;
   phipm_status st = check_operator(h, A_host, nnz_model);
   if (st != PHIPM_OK) return st;
+  if (A_host->kind == PHIPM_OP_FUNCTION) return fail(h, PHIPM_EINVAL, "host-buffer solve: CSR or stencil operators");
   if (p < 0 || p > PHIPM_P_MAX) return fail(h, PHIPM_EINVAL, "p out of [0, 8]");
   const int n = op_n(A_host);
   if (n > 0 && (!b_host || !u_host)) return fail(h, PHIPM_EINVAL, "b or u is NULL");
@@ -1071,7 +1107,7 @@ extern "C" phipm_status phipm_probe_phase_ticks(phipm_handle* h, unsigned long l
 #endif
 
 extern "C" int32_t phipm_team_for(const phipm_handle* h, int32_t precision, int32_t kind, int32_t n) {
-  if (!h || precision < 0 || precision > 2 || (kind != 0 && kind != 1) || n <= 0) return 0;
+  if (!h || precision < 0 || precision > 2 || kind < 0 || kind > 2 || n <= 0) return 0;
   return choose_team(h, precision, kind, n);
 }
 
@@ -1146,7 +1182,7 @@ extern "C" phipm_status phipm_tune_load(phipm_handle* h, const char* path) {
       add_batch[(int)(pr * 10000 + lc * 100 + lg)] = {(int)tm, 0.0};
     } else {
       if (!json_int(obj, "precision", pr) || !json_int(obj, "kind", kd) || !json_int(obj, "log2n", lg) ||
-          !json_int(obj, "team", tm) || pr < 0 || pr > 2 || kd < 0 || kd > 1 || lg < 0 || lg > 30 || tm < 1 ||
+          !json_int(obj, "team", tm) || pr < 0 || pr > 2 || kd < 0 || kd > 2 || lg < 0 || lg > 30 || tm < 1 ||
           tm > 1 << 20)
         return fail(h, PHIPM_EINVAL, "tuning cache: malformed entry");
       add[(int)(pr * 10000 + kd * 1000 + lg)] = {(int)tm, 0.0};

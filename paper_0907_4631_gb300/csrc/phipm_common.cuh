@@ -24,7 +24,7 @@
 #define PM_ENOTRUN 9      // batched: the launch stopped before a team took this problem
 
 struct DevOp {
-  int kind;          // 0 CSR, 1 stencil
+  int kind;          // 0 CSR, 1 stencil, 2 built-in function (matrix-free)
   int n;
   long long nnz;     // structural nonzeros (cost model, Eq. 4)
   const int* rowptr;
@@ -36,8 +36,11 @@ struct DevOp {
   double cc, cm[3], cp[3];
   df32 cc2, cm2[3], cp2[3];   // stencil coefficients as float pairs (hi alone for FP32)
   int quad;                   // stencil with nx a multiple of 4: rows taken four at a time
-  int pad_;
+  int fn;                     // kind 2 (matrix-free): built-in function id
   unsigned long long mnx, mny;   // multiply-high divisors by nx and ny (pm_udiv; 0 for 1)
+  const double* fld[4];       // kind 2: the function's fields (device arrays, may be null)
+  double fsc[6];              // kind 2: the function's scalars
+  double fnorm;               // kind 2: caller's bound of ||A||_inf (<= 0: computed)
 };
 
 // x / d for 0 <= x < 2^32 as the high word of x * m, m = floor((2^64 - 1) / d) + 1 for

@@ -286,8 +286,43 @@ template <class S, bool CG> struct DLoadAs {      // FP64 vector read as S
   }
 };
 
+// Row r of a built-in matrix-free operator (kind 2) applied to x (an index -> double
+// loader), in FP64; with asum, also the row's sum of absolute entries (for ||A||_inf).
+// PHIPM_FN_VARCOEF_CONVDIFF (include/phipm.h): for each dimension d, the diffusion
+// fluxes through the two faces with face diffusivities (kappa_i + kappa_nb) / 2
+// (kappa_i at the boundary, where x is 0) and the central-difference convection term.
+template <class XF>
+__device__ __forceinline__ double fn_row(const DevOp& A, int r, const XF& x, double* asum) {
+  const int nx = A.nx, ny = A.ny;
+  const unsigned line = pm_udiv((unsigned)r, A.mnx);
+  const int c[3] = {r - (int)line * nx, (A.ndim > 1) ? (int)line - (int)pm_udiv(line, A.mny) * ny : 0,
+                    (A.ndim > 2) ? (int)pm_udiv(line, A.mny) : 0};
+  const int ext[3] = {nx, ny, A.nz};
+  const int stride[3] = {1, nx, nx * ny};
+  const double* kap = A.fld[0];
+  const double k0 = kap[r], xr = x(r);
+  double acc = 0.0, as = 0.0;
+  for (int d = 0; d < A.ndim; ++d) {
+    const bool hm = c[d] > 0, hp = c[d] < ext[d] - 1;
+    const double xm = hm ? x(r - stride[d]) : 0.0, xp = hp ? x(r + stride[d]) : 0.0;
+    const double km = hm ? 0.5 * (k0 + kap[r - stride[d]]) : k0;
+    const double kp = hp ? 0.5 * (k0 + kap[r + stride[d]]) : k0;
+    const double sd = A.fsc[d], cd = A.fsc[3 + d];
+    const double v = A.fld[1 + d] ? A.fld[1 + d][r] : 0.0;
+    acc += sd * (kp * (xp - xr) - km * (xr - xm)) - cd * v * (xp - xm);
+    if (asum) {
+      as += sd * (kp + km);
+      if (hp) as += fabs(sd * kp - cd * v);
+      if (hm) as += fabs(sd * km + cd * v);
+    }
+  }
+  if (asum) *asum = as;
+  return acc;
+}
+
 template <class S, class XL>
 __device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
+  if (A.kind == 2) return Elem<S>::from_d(fn_row(A, r, [&](int i) { return Elem<S>::to_d(x(i)); }, nullptr));
   if constexpr (Elem<S>::kind == 0) {
     double acc = 0.0;
     if (A.kind == 0) {
@@ -582,7 +617,7 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
     }
   } else {
     if constexpr (IsVecLoad<XL>::value) {
-      if (A.quad) {
+      if (A.kind == 1 && A.quad) {
         stencil_rows4<S, IsVecLoad<XL>::cg>(A, x.p, out, sc, scale, lo, hi);
         return;
       }
@@ -1631,6 +1666,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
   {
     double na = 0.0, nb0 = 0.0, nball = 0.0, asym = 0.0;
     for (int r = lo + tid; r < hi; r += nth) {
+      if (P.A.kind == 2 && !(P.A.fnorm > 0.0)) {    // matrix-free, no bound given: row sums
+        double rs = 0.0;
+        fn_row(P.A, r, [&](int i) { return 0.0; }, &rs);
+        na = fmax(na, rs);
+      }
       if (P.A.kind == 0) {
         const int k0 = P.A.rowptr[r], k1 = P.A.rowptr[r + 1];
         double rs = 0.0;
@@ -1669,6 +1709,8 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     double normA;
     if (P.A.kind == 0) {
       normA = s.coef[0];
+    } else if (P.A.kind == 2) {
+      normA = (P.A.fnorm > 0.0) ? P.A.fnorm : s.coef[0];
     } else {
       normA = fabs(P.A.cc);
       for (int d = 0; d < P.A.ndim; ++d) normA += fabs(P.A.cm[d]) + fabs(P.A.cp[d]);
@@ -1677,6 +1719,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
     bool symmetric;
     if (P.symm >= 0) symmetric = P.symm != 0;
     else if (P.A.kind == 0) symmetric = s.coef[3] == 0.0;
+    else if (P.A.kind == 2) symmetric = false;    // a function's symmetry is not detected (symm = 1 declares it)
     else {
       symmetric = true;
       for (int d = 0; d < P.A.ndim; ++d) symmetric = symmetric && (P.A.cm[d] == P.A.cp[d]);

@@ -19,7 +19,8 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, EMAXSTEPS, ETIMEOUT, EBOUNDS, ETOOLARGE, ENOTRUN = range(10)
 F64, F32_MIXED, F64_PAIR = 0, 1, 2
-OP_CSR, OP_STENCIL = 0, 1
+OP_CSR, OP_STENCIL, OP_FUNCTION = 0, 1, 2
+FN_VARCOEF_CONVDIFF = 0
 CTRL_PAPER, CTRL_LEARNED, CTRL_FIXED_M, CTRL_LEARNED_STEPS = 0, 1, 2, 3      # phipm_controller
 M_MAX, P_MAX, NOALLOC_MAX_N = 64, 8, 8192
 MLP_PARAMS, CONTROLLER_FLOATS = 4866, 4886
@@ -34,8 +35,14 @@ class StencilC(ctypes.Structure):
                 ("c_minus", c_double * 3), ("c_plus", c_double * 3)]
 
 
+class FunctionC(ctypes.Structure):
+    _fields_ = [("fn", c_int32), ("ndim", c_int32), ("nx", c_int32), ("ny", c_int32), ("nz", c_int32),
+                ("reserved", c_int32), ("field", c_void_p * 4), ("scal", c_double * 6), ("norm_inf", c_double),
+                ("cost", c_int64)]
+
+
 class OperatorC(ctypes.Structure):
-    _fields_ = [("kind", c_int32), ("csr", CsrC), ("st", StencilC)]
+    _fields_ = [("kind", c_int32), ("csr", CsrC), ("st", StencilC), ("fn", FunctionC)]
 
 
 class StatsC(ctypes.Structure):
@@ -166,7 +173,13 @@ class DeviceOperator:
         import torch
         self.src = op
         self.c = OperatorC()
-        if hasattr(op, "rowptr"):
+        if hasattr(op, "fields"):              # a built-in matrix-free function with its data
+            self.fields = [None if f is None else torch.as_tensor(np.ascontiguousarray(f, dtype=np.float64)).to(device)
+                           for f in op.fields]
+            self.c.kind = OP_FUNCTION
+            self.c.fn = function_c(op, [0 if f is None else f.data_ptr() for f in self.fields])
+            self.n = int(op.n)
+        elif hasattr(op, "rowptr"):
             if arrays is not None:
                 self.rowptr, self.colind, self.values = arrays
             else:
@@ -181,6 +194,21 @@ class DeviceOperator:
             self.c.kind = OP_STENCIL
             self.c.st = stencil_c(op)
             self.n = int(op.n)
+
+
+def function_c(op, ptrs) -> FunctionC:
+    """The C descriptor of a matrix-free operator object (fn id, grid, scalars, optional
+    norm bound and cost) with its fields at the given device addresses."""
+    c = FunctionC()
+    c.fn = int(op.fn)
+    c.ndim, c.nx, c.ny, c.nz = int(op.ndim), int(op.nx), int(op.ny), int(op.nz)
+    for d in range(4):
+        c.field[d] = ptrs[d] if d < len(ptrs) else 0
+    for d in range(6):
+        c.scal[d] = float(op.scal[d])
+    c.norm_inf = float(getattr(op, "norm_bound", 0.0))
+    c.cost = int(getattr(op, "cost", 0))
+    return c
 
 
 def stencil_c(st) -> StencilC:

@@ -131,6 +131,66 @@ def convection_diffusion_2d(N: int, d: float, vx: float, vy: float) -> Stencil:
     return Stencil(2, N, N, 1, -4.0 * dd, cm, cp)
 
 
+@dataclasses.dataclass
+class VarCoefConvDiff:
+    """Data of the built-in matrix-free operator PHIPM_FN_VARCOEF_CONVDIFF (include/phipm.h):
+    a grid, the diffusivity field kappa (n values > 0), velocity fields (n values each, or
+    None) and the scalars 1/h^2 and 1/(2h) per dimension.  Only inputs: the product itself
+    runs in the library's kernels (and, separately, in the oracle)."""
+    ndim: int
+    nx: int
+    ny: int
+    nz: int
+    kappa: np.ndarray
+    vel: list                      # ndim entries, arrays or None
+    h: float
+    norm_bound: float = 0.0        # <= 0: the library computes ||A||_inf on the device
+    cost: int = 0                  # <= 0: the grid operator's structural nonzeros
+    fn: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def fields(self) -> list:
+        return [self.kappa] + [self.vel[d] if d < len(self.vel) else None for d in range(3)]
+
+    @property
+    def scal(self) -> list:
+        s2 = [1.0 / (self.h * self.h) if d < self.ndim else 0.0 for d in range(3)]
+        s1 = [1.0 / (2.0 * self.h) if d < self.ndim else 0.0 for d in range(3)]
+        return s2 + s1
+
+
+def varcoef_convdiff(ndim: int, N: int, speed: float, seed: int, kappa_amp: float = 0.5) -> VarCoefConvDiff:
+    """A smooth positive diffusivity 1 + kappa_amp sin(2 pi x) cos(pi y) (cos(pi z) in 3D)
+    plus a small seeded perturbation, and, for speed > 0, a rotating velocity field of that
+    magnitude, v = speed (cos(pi y), sin(pi x)[, cos(pi x)]), on the N^ndim interior grid,
+    h = 1 / (N + 1)."""
+    h = 1.0 / (N + 1)
+    g = np.arange(1, N + 1) * h
+    dims = [N] * ndim + [1] * (3 - ndim)
+    z, y, x = np.meshgrid(g if ndim > 2 else [0.5], g if ndim > 1 else [0.5], g, indexing="ij")
+    n = N ** ndim
+    kap = 1.0 + kappa_amp * np.sin(2 * np.pi * x) * np.cos(np.pi * y) * (np.cos(np.pi * z) if ndim > 2 else 1.0)
+    kap = kap.reshape(-1) * (1.0 + 0.05 * uniform(seed, 7, n, -1.0, 1.0))
+    vel = [None] * ndim
+    if speed > 0:
+        comps = [np.cos(np.pi * y), np.sin(np.pi * x), np.cos(np.pi * x)]
+        vel = [speed * comps[d].reshape(-1) for d in range(ndim)]
+    return VarCoefConvDiff(ndim, dims[0], dims[1], dims[2], kap, vel, h)
+
+
+def varcoef_convdiff_problem(ndim: int = 2, N: int = 64, speed: float = 20.0, p: int = 2, t_end: float = 1e-3,
+                             tol: float = 1e-8, seed: int = 6000) -> Problem:
+    """A matrix-free phipm problem (Sec. 3.5): the variable-coefficient operator above,
+    b_k ~ N(0, 1)."""
+    op = varcoef_convdiff(ndim, N, speed, seed)
+    return Problem(f"varcoef_{ndim}d_{N}", op, _normal_vectors(seed, op.n, p + 1), t_end, tol,
+                   1 if speed == 0 else 0, meta=dict(seed=seed))
+
+
 def stencil_to_csr(st: Stencil) -> CSR:
     """Assemble the CSR matrix of a stencil (columns sorted within each row)."""
     n = st.n

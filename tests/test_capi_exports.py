@@ -34,7 +34,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     """sizeof / offsetof of every ABI struct, from the C compiler, equal the ctypes mirror."""
     import os
     import subprocess
-    structs = {"phipm_csr": pm.CsrC, "phipm_stencil": pm.StencilC, "phipm_operator": pm.OperatorC,
+    structs = {"phipm_csr": pm.CsrC, "phipm_stencil": pm.StencilC, "phipm_function": pm.FunctionC,
+               "phipm_operator": pm.OperatorC,
                "phipm_stats": pm.StatsC, "phipm_params": pm.ParamsC, "phipm_trace_record": pm.TraceRecordC,
                "phipm_tune_entry": pm.TuneEntryC}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "phipm.h"', "int main(void) {"]
