@@ -62,7 +62,9 @@ struct PmShared {
   int perm[PM_NA];                     // the row interchanges of the LU as one permutation
   float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
-  alignas(16) unsigned char zw[PM_ZW_BYTES];   // this CTA's rows of z and A z during a dot pass
+  unsigned long long mbar;             // completion barrier of the stencil product's bulk copy
+  alignas(16) unsigned char zw[PM_ZW_BYTES];   // this CTA's rows of z and A z during a dot pass;
+                                               // the stencil product's staged rows during a product
 };
 
 struct PmWork {
@@ -469,6 +471,57 @@ __device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, con
   }
 }
 
+// ------------------------------------------------------------------------------------
+// staging of a stencil product's rows through the TMA bulk-copy engine
+// ------------------------------------------------------------------------------------
+struct Stage {
+  unsigned char* buf;            // shared memory, 16-byte aligned, PM_ZW_BYTES
+  unsigned long long* mbar;      // the CTA's mbarrier (initialised by phipm_device)
+  unsigned* phase;               // how many phases of it this thread has waited for
+  long long timeout;             // bound of the wait, clock64 cycles
+};
+
+__device__ __forceinline__ unsigned pm_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void pm_mbar_init(unsigned long long* mbar) {   // thread 0; a __syncthreads follows
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.mbarrier_init.release.cluster;"
+               :: "r"(pm_smem_addr(mbar)) : "memory");
+}
+
+// x[a, b) into stg.buf by one bulk asynchronous copy (cp.async.bulk) that completes on
+// the mbarrier; every thread waits for that phase, bounded by stg.timeout.  Returns the
+// same answer in every thread of the CTA: false if some thread's wait gave up.  The
+// addresses and the size must be multiples of 16 bytes (the caller checks).  x was written
+// by generic stores of this launch (this CTA's and, before a team barrier, other CTAs'):
+// every thread orders its generic accesses of global and shared memory before the
+// copy's async-proxy accesses with proxy fences, ahead of the barrier that precedes the
+// copy's issue.
+template <class S>
+__device__ bool stage_rows(const Stage& stg, const S* x, int a, int b) {
+  const unsigned bytes = (unsigned)(b - a) * (unsigned)sizeof(S);
+  const unsigned mb = pm_smem_addr(stg.mbar);
+  asm volatile("fence.proxy.async.global;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();                                    // earlier readers of the buffer are done
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(pm_smem_addr(stg.buf)), "l"(x + a), "r"(bytes), "r"(mb) : "memory");
+  }
+  const unsigned par = *stg.phase & 1u;
+  *stg.phase += 1;
+  bool ok = false;
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(mb), "r"(par) : "memory");
+    if (done) { ok = true; break; }
+    if (clock64() - t0 > stg.timeout) break;
+  }
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 // One stencil row from its centre value and six neighbours (zero where the
 // neighbour is outside the grid, which adds nothing), in spmv_row's order.
 template <class S>
@@ -509,24 +562,44 @@ __device__ __forceinline__ S stencil_point(const DevOp& A, S xc, S xl, S xr, S y
 // team) are read through L2; every quad lies wholly inside or outside, since lo, hi,
 // nx and nx ny are multiples of 4.
 template <class S, bool CG, class Epi>
-__device__ __forceinline__ void stencil_rows4_epi(const DevOp& A, const S* __restrict__ x, int lo, int hi,
-                                                  const Epi& epi) {
+__device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __restrict__ x, int lo, int hi,
+                                                  const Epi& epi, const Stage* stg = nullptr) {
   typedef Elem<S> E;
   const int nx = A.nx, ny = A.ny, nz = A.nz, pl = nx * ny;
   const int nq = (hi - lo) >> 2;
   const S zero = E::zero_elem();
+  // With a stage, the rows [sa, sb) = this CTA's rows and the grid lines next to them in
+  // y are copied into shared memory by the TMA engine when they fit; the x- and
+  // y-neighbours then come from shared memory and only the z-neighbour quads from L2.
+  // sa and sb are multiples of 4 rows (lo of 64, nx and n of 4), so the copy starts and
+  // ends on 16-byte boundaries.
+  int sa = 0, sb = 0;
+  const S* sx = nullptr;
+  if (stg != nullptr && hi > lo) {
+    sa = max(0, lo - nx);
+    sb = min(A.n, hi + nx);
+    if ((long long)(sb - sa) * (long long)sizeof(S) <= (long long)PM_ZW_BYTES) {
+      if (!stage_rows<S>(*stg, x, sa, sb)) return false;
+      sx = reinterpret_cast<const S*>(stg->buf) - sa;   // indexed by absolute row
+    } else {
+      sa = sb = 0;
+    }
+  }
+  auto staged = [&](int r) { return (unsigned)(r - sa) < (unsigned)(sb - sa); };
   auto outside = [&](int r) { return CG && (unsigned)(r - lo) >= (unsigned)(hi - lo); };
   auto ldq = [&](Quad<S>& q, int r, bool ok) {
     if (!ok) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) q.x[k] = zero;
+    } else if (staged(r)) {
+      q.load(sx + r);
     } else if (outside(r)) {
       q.load_cg(x + r);
     } else {
       q.load(x + r);
     }
   };
-  auto lds = [&](int r, bool ok) -> S { return !ok ? zero : outside(r) ? ld_cg(x + r) : x[r]; };
+  auto lds = [&](int r, bool ok) -> S { return !ok ? zero : staged(r) ? sx[r] : outside(r) ? ld_cg(x + r) : x[r]; };
   constexpr int U = sizeof(S) == 4 ? 2 : 1;
   for (int q0 = threadIdx.x; q0 < nq; q0 += U * blockDim.x) {
     Quad<S> c[U], ym[U], yp[U], zm[U], zp[U];
@@ -569,6 +642,7 @@ __device__ __forceinline__ void stencil_rows4_epi(const DevOp& A, const S* __res
   }
   VecLoad<S, CG> xl{x, lo, hi};
   for (int r = lo + 4 * nq + threadIdx.x; r < hi; r += blockDim.x) epi.row(r, spmv_row<S>(A, r, xl));
+  return true;
 }
 
 // epilogue of a plain product: out = (A x) * sc (scale) or A x
@@ -588,9 +662,10 @@ struct StoreScaled {
 };
 
 template <class S, bool CG>
-__device__ __forceinline__ void stencil_rows4(const DevOp& A, const S* __restrict__ x, S* __restrict__ out,
-                                              typename Elem<S>::Coef sc, bool scale, int lo, int hi) {
-  stencil_rows4_epi<S, CG>(A, x, lo, hi, StoreScaled<S>{out, sc, scale});
+__device__ __forceinline__ bool stencil_rows4(const DevOp& A, const S* __restrict__ x, S* __restrict__ out,
+                                              typename Elem<S>::Coef sc, bool scale, int lo, int hi,
+                                              const Stage* stg) {
+  return stencil_rows4_epi<S, CG>(A, x, lo, hi, StoreScaled<S>{out, sc, scale}, stg);
 }
 
 template <class XL> struct IsVecLoad { static constexpr bool value = false; };
@@ -603,8 +678,9 @@ template <class S, bool CG> struct IsVecLoad<VecLoad<S, CG>> {
 // stencil rows two at a time too: their neighbour loads are independent, so a pass has
 // both rows' loads in flight instead of paying the load latency once per row)
 template <class S, class XL>
-__device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __restrict__ out,
-                                          typename Elem<S>::Coef sc, bool scale, int lo, int hi) {
+__device__ __forceinline__ bool spmv_rows(const DevOp& A, const XL& x, S* __restrict__ out,
+                                          typename Elem<S>::Coef sc, bool scale, int lo, int hi,
+                                          const Stage* stg = nullptr) {
   typedef Elem<S> E;
   const int nth = blockDim.x;
   if (A.kind == 0) {
@@ -617,10 +693,7 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
     }
   } else {
     if constexpr (IsVecLoad<XL>::value) {
-      if (A.kind == 1 && A.quad) {
-        stencil_rows4<S, IsVecLoad<XL>::cg>(A, x.p, out, sc, scale, lo, hi);
-        return;
-      }
+      if (A.kind == 1 && A.quad) return stencil_rows4<S, IsVecLoad<XL>::cg>(A, x.p, out, sc, scale, lo, hi, stg);
     }
     for (int r = lo + threadIdx.x; r < hi; r += 2 * nth) {
       const int r2 = r + nth;
@@ -630,6 +703,7 @@ __device__ __forceinline__ void spmv_rows(const DevOp& A, const XL& x, S* __rest
       if (r2 < hi) out[r2] = scale ? E::scale(y1, sc) : y1;
     }
   }
+  return true;
 }
 
 // epilogue of a w-recurrence product, Eq. (wrecurrence): w_j = A w_{j-1} +
@@ -1619,7 +1693,7 @@ __device__ __forceinline__ void set_inv(PmScal& c, double x) {   // thread 0: 1/
 #define PM_ATT_FAIL 3      // status set
 
 template <class Team, class S>
-__device__ void phipm_device(const Team& team, const DevProblem& P, const DevParams& prm, DevResult& res,
+__device__ __forceinline__ void phipm_device(const Team& team, const DevProblem& P, const DevParams& prm, DevResult& res,
                              PmShared& s, const PmWork& w) {
   typedef Elem<S> E;
   typedef typename E::Coef C;
@@ -1642,6 +1716,10 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
 #ifdef PM_PHASE_PROBE
   long long pm_t_last = clock64();
 #endif
+  // the stencil products stage their rows through the TMA engine (stage_rows)
+  unsigned tma_phase = 0;
+  const Stage stg{s.zw, &s.mbar, &tma_phase, prm.timeout_cycles};
+  if (tid == 0) pm_mbar_init(&s.mbar);
   for (int e = tid; e < (PM_MAXM + 1) * PM_MAXM; e += nth) s.H[e] = 0.0;
   if (tid == 0) {
     c.status = PM_OK;
@@ -1660,6 +1738,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
 // already accumulated in that format)
 #define PM_SUM_OR_FAIL(K) do { if (!team_sum<false>(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 #define PM_BSUM_OR_FAIL(K) do { if (!team_sum<(Elem<S>::kind != 0)>(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
+#define PM_SPMV_OR_FAIL(call) do { if (!(call)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 #define PM_MAX_OR_FAIL(K) do { if (!team_max(team, s, (K), w, parity)) { if (tid == 0) c.status = PM_ETIMEOUT; goto done; } } while (0)
 
   // ---------------- setup (a1): ||A||_inf, ||b_0||_inf, max_k ||b_k||_inf, symmetry; u = b_0
@@ -1772,7 +1851,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
       VecLoad<double, Team::multi> xl{xin, lo, hi};
       WEpi we{wout, P.b + j, c.tl, p - j, j == p, 0.0};
       if (P.A.kind == 1 && P.A.quad) {
-        stencil_rows4_epi<double, Team::multi>(P.A, xin, lo, hi, we);
+        PM_SPMV_OR_FAIL((stencil_rows4_epi<double, Team::multi>(P.A, xin, lo, hi, we, &stg)));
       } else {
         for (int r = lo + tid; r < hi; r += nth) we.row(r, spmv_row<double>(P.A, r, xl));
       }
@@ -1906,7 +1985,7 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               spmv_rows<S>(P.A, xl, Wv, sc, true, lo, hi);
             } else {
               VecLoad<S, Team::multi> xl{zp, lo, hi};
-              spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi);
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi, &stg));
             }
             matvecs += 1;
             kry_steps += 1;
@@ -2110,11 +2189,11 @@ __device__ void phipm_device(const Team& team, const DevProblem& P, const DevPar
               spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
             } else if (j == j0) {
               VecLoad<S, Team::multi> xl{V + (size_t)j * ld, lo, hi};   // v_j normalised at the end of the previous extension
-              spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi);
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi, &stg));
             } else {
               VecLoad<S, Team::multi> xl{yprev, lo, hi};
               for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
-              spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, &stg));
             }
             matvecs += 1;
             kry_steps += 1;
@@ -2434,4 +2513,5 @@ done:
 #undef PM_SUM_OR_FAIL
 #undef PM_BSUM_OR_FAIL
 #undef PM_MAX_OR_FAIL
+#undef PM_SPMV_OR_FAIL
 }
