@@ -163,6 +163,11 @@ typedef struct {
   int32_t controller;     /* phipm_controller: 0 = the paper's controller; 1, 3 = learned
                              proposals (see below); 2 = fixed Krylov dimension (phip) */
   int64_t timeout_cycles; /* bound on every device-side spin-wait, in clock64 cycles */
+  int32_t stencil_stage;  /* 1: a stencil product first copies the CTA's rows and the grid
+                             lines next to them into shared memory with one TMA bulk copy
+                             (when they fit 64 KB); 0 (default): it reads them as 16-byte
+                             quads through L1, measured faster on GB300 */
+  int32_t reserved;
 } phipm_params;
 
 /* Controllers.  PHIPM_CTRL_FIXED_M is the fixed-dimension variant the paper

@@ -137,6 +137,8 @@ extern "C" void phipm_default_params(phipm_params* o) {
   o->precision = PHIPM_F64;
   o->controller = 0;
   o->timeout_cycles = 20000000000ll;   // about 10 s at 2 GHz
+  o->stencil_stage = 0;
+  o->reserved = 0;
 }
 
 static bool params_ok(const phipm_params& p, std::string& why) {
@@ -151,6 +153,7 @@ static bool params_ok(const phipm_params& p, std::string& why) {
   }
   if (p.controller < 0 || p.controller > 3) { why = "unknown controller"; return false; }
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
+  if (p.stencil_stage != 0 && p.stencil_stage != 1) { why = "stencil_stage must be 0 or 1"; return false; }
   return true;
 }
 
@@ -265,6 +268,7 @@ static DevParams make_params(const phipm_params& p) {
   d.m_max = p.m_max;
   d.fixed_m = (p.controller == PHIPM_CTRL_FIXED_M) ? 1 : 0;
   d.mlp_every_step = (p.controller == PHIPM_CTRL_LEARNED_STEPS) ? 1 : 0;
+  d.stencil_stage = p.stencil_stage;
   d.max_steps = p.max_steps;
   d.max_rejects = p.max_rejects;
   d.timeout_cycles = p.timeout_cycles;

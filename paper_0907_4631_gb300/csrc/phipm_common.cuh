@@ -64,6 +64,8 @@ struct DevParams {
   int mlp_every_step;    // 1: the learned controller proposes the first attempt of every step
   long long max_steps, max_rejects;
   long long timeout_cycles;
+  int stencil_stage;     // 1: stencil products stage their rows through the TMA engine
+  int pad1;
   double pade_b[14];     // degree-13 Pade coefficients, computed on the host from their closed form
   const float* mlp;      // learned-controller blob (device), or null
   TraceRec* trace;       // attempt records (device), or null

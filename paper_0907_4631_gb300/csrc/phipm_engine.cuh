@@ -1718,7 +1718,8 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
 #endif
   // the stencil products stage their rows through the TMA engine (stage_rows)
   unsigned tma_phase = 0;
-  const Stage stg{s.zw, &s.mbar, &tma_phase, prm.timeout_cycles};
+  const Stage stage{s.zw, &s.mbar, &tma_phase, prm.timeout_cycles};
+  const Stage* stg = prm.stencil_stage ? &stage : nullptr;
   if (tid == 0) pm_mbar_init(&s.mbar);
   for (int e = tid; e < (PM_MAXM + 1) * PM_MAXM; e += nth) s.H[e] = 0.0;
   if (tid == 0) {
@@ -1851,7 +1852,7 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
       VecLoad<double, Team::multi> xl{xin, lo, hi};
       WEpi we{wout, P.b + j, c.tl, p - j, j == p, 0.0};
       if (P.A.kind == 1 && P.A.quad) {
-        PM_SPMV_OR_FAIL((stencil_rows4_epi<double, Team::multi>(P.A, xin, lo, hi, we, &stg)));
+        PM_SPMV_OR_FAIL((stencil_rows4_epi<double, Team::multi>(P.A, xin, lo, hi, we, stg)));
       } else {
         for (int r = lo + tid; r < hi; r += nth) we.row(r, spmv_row<double>(P.A, r, xl));
       }
@@ -1985,7 +1986,7 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
               spmv_rows<S>(P.A, xl, Wv, sc, true, lo, hi);
             } else {
               VecLoad<S, Team::multi> xl{zp, lo, hi};
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi, &stg));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi, stg));
             }
             matvecs += 1;
             kry_steps += 1;
@@ -2189,11 +2190,11 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
               spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
             } else if (j == j0) {
               VecLoad<S, Team::multi> xl{V + (size_t)j * ld, lo, hi};   // v_j normalised at the end of the previous extension
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi, &stg));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi, stg));
             } else {
               VecLoad<S, Team::multi> xl{yprev, lo, hi};
               for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, &stg));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, stg));
             }
             matvecs += 1;
             kry_steps += 1;

@@ -313,3 +313,27 @@ def test_batched_graph_replay_sees_new_inputs():
     for p_, u, t, tl in zip(probs, us, t2, tol2):
         ref, _ = O.phipm(t, p_.op, [-0.5 * x for x in p_.b], tl, 0)
         assert _rel(u.cpu().numpy(), ref) <= TOL64
+
+
+@pytest.mark.parametrize("prec,case", [("f64", "lap2d_32"), ("f64pair", "lap2d_150"), ("f32", "lap3d_40"),
+                                       ("f64", "lap3d_24")])
+def test_stencil_rows_staged_by_tma(prec, case):
+    """params.stencil_stage = 1: each stencil product first copies the CTA's rows and the
+    grid lines next to them in y into shared memory with one TMA bulk copy (when they fit),
+    on one CTA and on the grid; results against the sine expansion."""
+    s = pm.Phipm(prec, stencil_stage=1)
+    if case == "lap2d_32":
+        pr = wl.laplacian_2d_problem()
+        ndim, N = 2, 32
+    elif case == "lap2d_150":
+        pr = wl.laplacian_2d_problem(N=150, p=2, t_end=2e-3, tol=1e-8, seed=1151)
+        ndim, N = 2, 150
+    elif case == "lap3d_40":
+        pr = wl.laplacian_3d_problem(N=40, p=2, t_end=1e-4, tol=1e-5, seed=3040)
+        ndim, N = 3, 40
+    else:
+        pr = wl.laplacian_3d_problem(N=24, p=2, t_end=1e-4, tol=1e-8, seed=3024)
+        ndim, N = 3, 24
+    u, st = _gpu(s, pr, symm=-1)
+    truth = T.solution_laplacian(ndim, N, pr.b, pr.t_end)
+    assert _rel(u, truth) <= (TOL32 if prec == "f32" else TOL64)
