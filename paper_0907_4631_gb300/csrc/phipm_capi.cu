@@ -285,6 +285,28 @@ static DevParams make_params(const phipm_params& p) {
     d.pade_b[j] = c;
     c = c * (double)(13 - j) / ((double)(26 - j) * (double)(j + 1));
   }
+  // degree-18 Taylor form: 1/k!, and the largest theta with sum_{k>18} theta^k / k! <=
+  // 2^-53 e^-theta (the truncated tail relative to the smallest possible |exp|), by bisection
+  double f = 1.0;
+  for (int k = 0; k <= 18; ++k) {
+    d.taylor_c[k] = f;
+    f /= (double)(k + 1);
+  }
+  auto tail = [](double th) {
+    double term = 1.0, sum = 0.0;
+    for (int k = 1; k <= 60; ++k) {
+      term *= th / (double)k;
+      if (k > 18) sum += term;
+    }
+    return sum;
+  };
+  double lo = 0.0, hi = 4.0;
+  for (int it = 0; it < 80; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (tail(mid) <= std::ldexp(1.0, -53) * std::exp(-mid)) lo = mid; else hi = mid;
+  }
+  d.taylor_theta = lo;
+  d.expm_taylor = 1;
   return d;
 }
 

@@ -1449,6 +1449,121 @@ __device__ __forceinline__ void mm_elems(double* C, const double* A, const doubl
   }
 }
 
+// squarings s = max(0, ceil(log2(||X||_1 / theta))) that bring ||X||_1 down to theta (Eq. 8)
+__device__ __forceinline__ int pm_squarings(double norm1, double theta) {
+  if (!(norm1 > theta)) return 0;
+  const double v = ceil(log2(norm1 / theta));
+  return v > 0 ? (int)v : 0;
+}
+
+// The squarings of the scaled exponential R (exp of the scaled augmented matrix) on the
+// team: sq - 1 full squarings (oth as scratch), the last one forming only columns ca
+// and cb; on return every CTA holds the top m entries of those columns in
+// s.phi0 / s.phi1.  out holds 2 PM_NA doubles of team-shared scratch.
+template <class Team>
+__device__ bool expm_square_out(const Team& team, PmShared& s, double* R, double* R2, double* out, int N, int m,
+                                int sq, int e0, int e1, int ca, int cb) {
+  const int G = team.size(), rk = team.rank();
+  double* cur = R;
+  double* oth = R2;
+  for (int q = 0; q + 1 < sq; ++q) {
+    mm_elems<Team::multi>(oth, cur, cur, N, e0, e1);
+    if (!team.sync()) return false;
+    double* t = cur; cur = oth; oth = t;
+  }
+  {
+    int r0, r1;
+    split_range(2 * N, rk, G, r0, r1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = r0 + warp; e < r1; e += PM_WARPS) {     // one warp per entry, lanes split k
+      const int which = e / N, i = e - which * N;
+      const int col = which ? cb : ca;
+      double v;
+      if (sq == 0) {
+        v = ldx<Team::multi>(&cur[i * PM_NA + col]);
+      } else {
+        double c0 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int k = lane + 32 * q;
+          if (k < N) c0 = fma(ldx<Team::multi>(&cur[i * PM_NA + k]), ldx<Team::multi>(&cur[k * PM_NA + col]), c0);
+        }
+        v = pm_warp_sum(c0);
+      }
+      if (lane == 0) out[which * PM_NA + i] = v;
+    }
+  }
+  if (!team.sync()) return false;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    s.phi0[i] = ldx<Team::multi>(&out[i]);
+    s.phi1[i] = ldx<Team::multi>(&out[PM_NA + i]);
+  }
+  __syncthreads();
+  return true;
+}
+
+// exp(H_hat) on a team of several CTAs by the degree-18 Taylor polynomial of
+// X = H_hat / 2^sq, sum_k X^k / k!, evaluated by Paterson-Stockmeyer with the powers
+// X, X^2, X^3, X^4 and four Horner steps in X^4, then sq squarings (sq from ||H_hat||_1
+// and theta, the largest norm whose truncation term stays below 2^-53 e^-theta).  Every
+// stage is a team-parallel matrix product followed by one team barrier; the Pade form
+// needs a pivoted LU and two triangular solves, sequences of N CTA-wide steps that
+// dominate a multi-CTA exponential.  One CTA keeps the Pade form (fewer products).
+// tc[k] = 1 / k!.  Same output as expm_team.
+template <class Team>
+__device__ bool expm_taylor_team(const Team& team, PmShared& s, const double* tc, double theta, double norm1,
+                                 double tau, int m, int p, double* ws, int ca, int cb) {
+  const int N = m + p + 1, NN = N * N;
+  const int G = team.size(), rk = team.rank();
+  const int sq = pm_squarings(norm1, theta);
+  double* X = ws;
+  double* X2 = ws + 1 * PM_NA2;
+  double* X3 = ws + 2 * PM_NA2;
+  double* X4 = ws + 3 * PM_NA2;
+  double* Y = ws + 4 * PM_NA2;
+  double* Y2 = ws + 5 * PM_NA2;
+  double* out = ws + PM_EXPM_MATS * PM_NA2;
+  int e0, e1;
+  split_range(NN, rk, G, e0, e1);
+  const double sc = ldexp(1.0, -sq);
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    double v = 0.0;
+    if (i < m && j < m) v = tau * s.H[i * PM_MAXM + j];
+    else if (i == 0 && j == m) v = 1.0;
+    else if (i >= m && j == i + 1) v = 1.0;
+    X[i * PM_NA + j] = v * sc;
+  }
+  if (!team.sync()) return false;
+  mm_elems<Team::multi>(X2, X, X, N, e0, e1);
+  if (!team.sync()) return false;
+  mm_elems<Team::multi>(X3, X2, X, N, e0, e1);
+  mm_elems<Team::multi>(X4, X2, X2, N, e0, e1);
+  __syncthreads();
+  // the top block B_4 = c16 I + c17 X + c18 X^2, then Y <- B_j + X^4 Y for j = 3 .. 0 with
+  // B_j = c_{4j} I + c_{4j+1} X + c_{4j+2} X^2 + c_{4j+3} X^3
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int i = e / N, j = e - i * N, o = i * PM_NA + j;
+    Y[o] = (i == j ? tc[16] : 0.0) + tc[17] * ldx<Team::multi>(&X[o]) + tc[18] * X2[o];
+  }
+  if (!team.sync()) return false;
+  double* cur = Y;
+  double* nxt = Y2;
+  for (int jb = 3; jb >= 0; --jb) {
+    mm_elems<Team::multi>(nxt, X4, cur, N, e0, e1);
+    __syncthreads();
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = e / N, j = e - i * N, o = i * PM_NA + j;
+      nxt[o] += (i == j ? tc[4 * jb] : 0.0) + tc[4 * jb + 1] * ldx<Team::multi>(&X[o]) + tc[4 * jb + 2] * X2[o] +
+                tc[4 * jb + 3] * X3[o];
+    }
+    if (!team.sync()) return false;
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  // squarings into the two matrices the products no longer need
+  return expm_square_out(team, s, cur, (cur == Y) ? Y2 : Y, out, N, m, sq, e0, e1, ca, cb);
+}
+
 // exp(H_hat) with H_hat = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]] (Eq. hathm,
 // size N = m+p+1), degree-13 Pade approximant (even/odd split) with sq
 // squarings (Sec. 3.1).  Products are split over the team by elements; every CTA
@@ -1456,8 +1571,11 @@ __device__ __forceinline__ void mm_elems(double* C, const double* A, const doubl
 // split by columns; only columns ca and cb of the last square are formed.
 // On return every CTA holds the top m entries of those columns in s.phi0/phi1.
 template <class Team>
-__device__ bool expm_team(const Team& team, PmShared& s, const double* bc, double tau, int m, int p, int sq,
-                          double* ws, int ca, int cb) {
+__device__ bool expm_team(const Team& team, PmShared& s, const DevParams& prm, double norm1, double tau, int m, int p,
+                          int sq, double* ws, int ca, int cb) {
+  if (Team::multi && team.size() > 1 && prm.expm_taylor)
+    return expm_taylor_team(team, s, prm.taylor_c, prm.taylor_theta, norm1, tau, m, p, ws, ca, cb);
+  const double* bc = prm.pade_b;
   const int N = m + p + 1, NN = N * N;
   const int G = team.size(), rk = team.rank();
   double* X = ws;
@@ -1608,50 +1726,9 @@ __device__ bool expm_team(const Team& team, PmShared& s, const double* bc, doubl
     }
   }
   if (!team.sync()) return false;
-  // squarings; the last one forms only columns ca and cb
-  double* cur = R;
-  double* oth = R2;
-  for (int q = 0; q + 1 < sq; ++q) {
-    mm_elems<Team::multi>(oth, cur, cur, N, e0, e1);
-    if (!team.sync()) return false;
-    double* t = cur; cur = oth; oth = t;
-  }
-  {
-    int r0, r1;
-    split_range(2 * N, rk, G, r0, r1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int e = r0 + warp; e < r1; e += PM_WARPS) {     // one warp per entry, lanes split k
-      const int which = e / N, i = e - which * N;
-      const int col = which ? cb : ca;
-      double v;
-      if (sq == 0) {
-        v = ldx<Team::multi>(&cur[i * PM_NA + col]);
-      } else {
-        double c0 = 0.0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int k = lane + 32 * q;
-          if (k < N) c0 = fma(ldx<Team::multi>(&cur[i * PM_NA + k]), ldx<Team::multi>(&cur[k * PM_NA + col]), c0);
-        }
-        v = pm_warp_sum(c0);
-      }
-      if (lane == 0) out[which * PM_NA + i] = v;
-    }
-  }
-  if (!team.sync()) return false;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    s.phi0[i] = ldx<Team::multi>(&out[i]);
-    s.phi1[i] = ldx<Team::multi>(&out[PM_NA + i]);
-  }
-  __syncthreads();
-  return true;
+  return expm_square_out(team, s, R, R2, out, N, m, sq, e0, e1, ca, cb);
 }
 
-__device__ __forceinline__ int pm_squarings(double norm1, double theta) {
-  if (!(norm1 > theta)) return 0;
-  const double v = ceil(log2(norm1 / theta));
-  return v > 0 ? (int)v : 0;
-}
 
 // ------------------------------------------------------------------------------------
 // the solver
@@ -2265,7 +2342,7 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
         const int mu = c.m_used;
         const int ca = (p >= 1) ? mu + p - 1 : 0;
         const int cb = mu + p;
-        if (!expm_team(team, s, prm.pade_b, c.tau_used, mu, p, c.sq, w.expm, ca, cb)) {
+        if (!expm_team(team, s, prm, c.norm1, c.tau_used, mu, p, c.sq, w.expm, ca, cb)) {
           if (tid == 0) c.status = PM_ETIMEOUT;
           goto done;
         }
