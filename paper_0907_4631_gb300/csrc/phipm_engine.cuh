@@ -561,9 +561,9 @@ __device__ __forceinline__ S stencil_point(const DevOp& A, S xc, S xl, S xr, S y
 // divisions (pm_udiv).  With CG, quads outside [lo, hi) (written by other CTAs of the
 // team) are read through L2; every quad lies wholly inside or outside, since lo, hi,
 // nx and nx ny are multiples of 4.
-template <class S, bool CG, class Epi>
-__device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __restrict__ x, int lo, int hi,
-                                                  const Epi& epi, const Stage* stg = nullptr) {
+template <class S, bool CG, bool STAGED, class Epi>
+__device__ __forceinline__ bool stencil_rows4_body(const DevOp& A, const S* __restrict__ x, int lo, int hi,
+                                                   const Epi& epi, const Stage* stg) {
   typedef Elem<S> E;
   const int nx = A.nx, ny = A.ny, nz = A.nz, pl = nx * ny;
   const int nq = (hi - lo) >> 2;
@@ -575,7 +575,7 @@ __device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __res
   // ends on 16-byte boundaries.
   int sa = 0, sb = 0;
   const S* sx = nullptr;
-  if (stg != nullptr && hi > lo) {
+  if (STAGED && hi > lo) {
     sa = max(0, lo - nx);
     sb = min(A.n, hi + nx);
     if ((long long)(sb - sa) * (long long)sizeof(S) <= (long long)PM_ZW_BYTES) {
@@ -585,7 +585,7 @@ __device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __res
       sa = sb = 0;
     }
   }
-  auto staged = [&](int r) { return (unsigned)(r - sa) < (unsigned)(sb - sa); };
+  auto staged = [&](int r) { return STAGED && (unsigned)(r - sa) < (unsigned)(sb - sa); };
   auto outside = [&](int r) { return CG && (unsigned)(r - lo) >= (unsigned)(hi - lo); };
   auto ldq = [&](Quad<S>& q, int r, bool ok) {
     if (!ok) {
@@ -643,6 +643,15 @@ __device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __res
   VecLoad<S, CG> xl{x, lo, hi};
   for (int r = lo + 4 * nq + threadIdx.x; r < hi; r += blockDim.x) epi.row(r, spmv_row<S>(A, r, xl));
   return true;
+}
+
+// the staged and the plain form are separate instances, so that the plain loop carries
+// no staging tests
+template <class S, bool CG, class Epi>
+__device__ __forceinline__ bool stencil_rows4_epi(const DevOp& A, const S* __restrict__ x, int lo, int hi,
+                                                  const Epi& epi, const Stage* stg = nullptr) {
+  if (stg != nullptr) return stencil_rows4_body<S, CG, true>(A, x, lo, hi, epi, stg);
+  return stencil_rows4_body<S, CG, false>(A, x, lo, hi, epi, nullptr);
 }
 
 // epilogue of a plain product: out = (A x) * sc (scale) or A x
