@@ -167,7 +167,12 @@ typedef struct {
                              lines next to them into shared memory with one TMA bulk copy
                              (when they fit 64 KB); 0 (default): it reads them as 16-byte
                              quads through L1, measured faster on GB300 */
-  int32_t reserved;
+  int32_t expm_pade;      /* 1: exp of the augmented matrix by the degree-13 Pade approximant
+                             with scaling and squaring (the paper's choice, Sec. 3.1); 0
+                             (default): by the degree-18 Taylor polynomial (Paterson-
+                             Stockmeyer) with scaling and squaring, no LU, faster on GB300.
+                             Both are accurate to about the unit roundoff; the cost model of
+                             Eq. (4) charges the Pade form either way. */
 } phipm_params;
 
 /* Controllers.  PHIPM_CTRL_FIXED_M is the fixed-dimension variant the paper

@@ -138,7 +138,7 @@ extern "C" void phipm_default_params(phipm_params* o) {
   o->controller = 0;
   o->timeout_cycles = 20000000000ll;   // about 10 s at 2 GHz
   o->stencil_stage = 0;
-  o->reserved = 0;
+  o->expm_pade = 0;
 }
 
 static bool params_ok(const phipm_params& p, std::string& why) {
@@ -154,6 +154,7 @@ static bool params_ok(const phipm_params& p, std::string& why) {
   if (p.controller < 0 || p.controller > 3) { why = "unknown controller"; return false; }
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
   if (p.stencil_stage != 0 && p.stencil_stage != 1) { why = "stencil_stage must be 0 or 1"; return false; }
+  if (p.expm_pade != 0 && p.expm_pade != 1) { why = "expm_pade must be 0 or 1"; return false; }
   return true;
 }
 
@@ -306,7 +307,7 @@ static DevParams make_params(const phipm_params& p) {
     if (tail(mid) <= std::ldexp(1.0, -53) * std::exp(-mid)) lo = mid; else hi = mid;
   }
   d.taylor_theta = lo;
-  d.expm_taylor = 1;
+  d.expm_taylor = p.expm_pade ? 0 : 1;
   return d;
 }
 

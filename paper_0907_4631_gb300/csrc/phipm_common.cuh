@@ -69,7 +69,7 @@ struct DevParams {
   double pade_b[14];     // degree-13 Pade coefficients, computed on the host from their closed form
   double taylor_c[19];   // 1 / k!, k <= 18 (the Taylor exponential of multi-CTA teams)
   double taylor_theta;   // largest ||X||_1 for which the degree-18 Taylor truncation term is below 2^-53 e^-||X||
-  int expm_taylor;       // 1: multi-CTA teams evaluate the exponential by the Taylor form
+  int expm_taylor;       // 1: the exponential by the degree-18 Taylor form; 0: the degree-13 Pade form
   int pad2;
   const float* mlp;      // learned-controller blob (device), or null
   TraceRec* trace;       // attempt records (device), or null

@@ -1511,14 +1511,15 @@ __device__ bool expm_square_out(const Team& team, PmShared& s, double* R, double
   return true;
 }
 
-// exp(H_hat) on a team of several CTAs by the degree-18 Taylor polynomial of
-// X = H_hat / 2^sq, sum_k X^k / k!, evaluated by Paterson-Stockmeyer with the powers
-// X, X^2, X^3, X^4 and four Horner steps in X^4, then sq squarings (sq from ||H_hat||_1
-// and theta, the largest norm whose truncation term stays below 2^-53 e^-theta).  Every
-// stage is a team-parallel matrix product followed by one team barrier; the Pade form
-// needs a pivoted LU and two triangular solves, sequences of N CTA-wide steps that
-// dominate a multi-CTA exponential.  One CTA keeps the Pade form (fewer products).
-// tc[k] = 1 / k!.  Same output as expm_team.
+// exp(H_hat) by the degree-18 Taylor polynomial of X = H_hat / 2^sq, sum_k X^k / k!,
+// evaluated by Paterson-Stockmeyer with the powers X, X^2, X^3, X^4 and four Horner
+// steps in X^4, then sq squarings (sq from ||H_hat||_1 and theta, the largest norm whose
+// truncation term stays below 2^-53 e^-theta).  Every stage is a team-parallel matrix
+// product followed by one team barrier.  The Pade form needs a pivoted LU and two
+// triangular solves, sequences of N CTA-wide steps, which cost more than the Taylor
+// form's extra product and squarings on grid and cluster teams (115 -> 50 us per
+// exponential on the 512^2 solve) and on one CTA too (709 -> 571 us per solve on the
+// 32^2 one).  tc[k] = 1 / k!.  Same output as expm_team's Pade form.
 template <class Team>
 __device__ bool expm_taylor_team(const Team& team, PmShared& s, const double* tc, double theta, double norm1,
                                  double tau, int m, int p, double* ws, int ca, int cb) {
@@ -1582,7 +1583,7 @@ __device__ bool expm_taylor_team(const Team& team, PmShared& s, const double* tc
 template <class Team>
 __device__ bool expm_team(const Team& team, PmShared& s, const DevParams& prm, double norm1, double tau, int m, int p,
                           int sq, double* ws, int ca, int cb) {
-  if (Team::multi && team.size() > 1 && prm.expm_taylor)
+  if (prm.expm_taylor)
     return expm_taylor_team(team, s, prm.taylor_c, prm.taylor_theta, norm1, tau, m, p, ws, ca, cb);
   const double* bc = prm.pade_b;
   const int N = m + p + 1, NN = N * N;

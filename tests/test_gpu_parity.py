@@ -337,3 +337,17 @@ def test_stencil_rows_staged_by_tma(prec, case):
     u, st = _gpu(s, pr, symm=-1)
     truth = T.solution_laplacian(ndim, N, pr.b, pr.t_end)
     assert _rel(u, truth) <= (TOL32 if prec == "f32" else TOL64)
+
+
+@pytest.mark.parametrize("team", [1, 4, 152])
+def test_pade_exponential_option_matches_the_oracle(team):
+    """params.expm_pade = 1: the exponential by the degree-13 Pade approximant, as the paper
+    computes it (the default is the degree-18 Taylor form); one CTA, a cluster, the grid."""
+    pr = wl.convdiff_2d_problem(N=130, p=3, t_end=1e-3, tol=1e-8, seed=2230)
+    ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    for pade in (0, 1):
+        s = pm.Phipm("f64", expm_pade=pade)
+        s.set_team(team)
+        u, st = _gpu(s, pr)
+        assert _rel(u, ref) <= TOL64
+        assert st["steps"] == rst.steps
