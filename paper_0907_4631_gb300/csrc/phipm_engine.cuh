@@ -19,7 +19,6 @@
 #define PM_ETA2 0.0625
 #define PM_DRED (PM_WARPS * (PM_NSLOT + 2))   // partials of a dot pass (vector x warp) or of a team fold
 #define PM_ZW_BYTES 65536                      // shared staging of the two vectors every product of a dot pass reads
-#define PM_RP_CACHE 4096                       // CSR row pointers of up to this many own rows kept in shared memory
 
 // Scalar state of one problem.  Thread 0 writes it, every thread reads it after
 // the next barrier: on GB300 a scalar FP64 expression evaluated by all threads
@@ -64,7 +63,6 @@ struct PmShared {
   float mh[2][MLP_H];                  // learned controller: hidden activations (warp 0)
   PmScal sc;
   unsigned long long mbar;             // completion barrier of the stencil product's bulk copy
-  int rp[PM_RP_CACHE + 1];             // this CTA's CSR row pointers (rowptr[lo .. hi]) for the whole solve
   alignas(16) unsigned char zw[PM_ZW_BYTES];   // this CTA's rows of z and A z during a dot pass;
                                                // the stencil product's staged rows during a product
 };
@@ -406,8 +404,7 @@ __device__ __forceinline__ S spmv_row(const DevOp& A, int r, const XL& x) {
 // take one round.  Arithmetic as in spmv_row.
 #define PM_CSR_U 6
 template <class S, class XL>
-__device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, const XL& x, S& y0, S& y1,
-                                              const int* rpc) {
+__device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, const XL& x, S& y0, S& y1) {
   typedef Elem<S> E;
   constexpr int kind = E::kind;
   typedef typename std::conditional<kind == 0, double, typename std::conditional<kind == 1, float, F2Acc>::type>::type
@@ -417,13 +414,11 @@ __device__ __forceinline__ void spmv_csr_pair(const DevOp& A, int r, int r2, con
   Acc c0, c1;
   if constexpr (kind == 2) { c0 = f2_zero(); c1 = f2_zero(); }
   else { c0 = 0; c1 = 0; }
-  // row extents from the shared-memory copy of this CTA's row pointers when there is
-  // one (rpc[r] = rowptr[r]), which saves a dependent L2 round trip per pass
-  const int a0 = rpc ? rpc[r] : __ldg(&A.rowptr[r]), b0 = rpc ? rpc[r + 1] : __ldg(&A.rowptr[r + 1]);
+  const int a0 = __ldg(&A.rowptr[r]), b0 = __ldg(&A.rowptr[r + 1]);
   int a1 = 0, b1 = 0;
   if (r2 >= 0) {
-    a1 = rpc ? rpc[r2] : __ldg(&A.rowptr[r2]);
-    b1 = rpc ? rpc[r2 + 1] : __ldg(&A.rowptr[r2 + 1]);
+    a1 = __ldg(&A.rowptr[r2]);
+    b1 = __ldg(&A.rowptr[r2 + 1]);
   }
   const int len = max(b0 - a0, b1 - a1);
   for (int t = 0; t < len; t += PM_CSR_U) {
@@ -694,14 +689,14 @@ template <class S, bool CG> struct IsVecLoad<VecLoad<S, CG>> {
 template <class S, class XL>
 __device__ __forceinline__ bool spmv_rows(const DevOp& A, const XL& x, S* __restrict__ out,
                                           typename Elem<S>::Coef sc, bool scale, int lo, int hi,
-                                          const Stage* stg = nullptr, const int* rpc = nullptr) {
+                                          const Stage* stg = nullptr) {
   typedef Elem<S> E;
   const int nth = blockDim.x;
   if (A.kind == 0) {
     for (int r = lo + threadIdx.x; r < hi; r += 2 * nth) {
       const int r2 = (r + nth < hi) ? r + nth : -1;
       S y0, y1;
-      spmv_csr_pair<S>(A, r, r2, x, y0, y1, rpc);
+      spmv_csr_pair<S>(A, r, r2, x, y0, y1);
       out[r] = scale ? E::scale(y0, sc) : y0;
       if (r2 >= 0) out[r2] = scale ? E::scale(y1, sc) : y1;
     }
@@ -1813,12 +1808,6 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
   const Stage stage{s.zw, &s.mbar, &tma_phase, prm.timeout_cycles};
   const Stage* stg = prm.stencil_stage ? &stage : nullptr;
   if (tid == 0) pm_mbar_init(&s.mbar);
-  // the CSR row pointers of this CTA's rows, read once for every product of the solve
-  const int* rpc = nullptr;
-  if (P.A.kind == 0 && hi - lo <= PM_RP_CACHE) {
-    for (int i = tid; i <= hi - lo; i += nth) s.rp[i] = P.A.rowptr[lo + i];
-    rpc = s.rp - lo;
-  }
   for (int e = tid; e < (PM_MAXM + 1) * PM_MAXM; e += nth) s.H[e] = 0.0;
   if (tid == 0) {
     c.status = PM_OK;
@@ -2081,10 +2070,10 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
               const C sc = scal_inv<S>(c);   // 1/beta
               DLoadAs<S, Team::multi> xl{wp, lo, hi};
               for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
-              spmv_rows<S>(P.A, xl, Wv, sc, true, lo, hi, nullptr, rpc);
+              spmv_rows<S>(P.A, xl, Wv, sc, true, lo, hi);
             } else {
               VecLoad<S, Team::multi> xl{zp, lo, hi};
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi, stg, rpc));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, Wv, scal_inv<S>(c), false, lo, hi, stg));
             }
             matvecs += 1;
             kry_steps += 1;
@@ -2285,14 +2274,14 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
             if (j == 0) {
               DLoadAs<S, Team::multi> xl{wp, lo, hi};
               for (int r = lo + tid; r < hi; r += nth) V[r] = E::from_d(wp[r] * c.inv);
-              spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, nullptr, rpc);
+              spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi);
             } else if (j == j0) {
               VecLoad<S, Team::multi> xl{V + (size_t)j * ld, lo, hi};   // v_j normalised at the end of the previous extension
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi, stg, rpc));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, false, lo, hi, stg));
             } else {
               VecLoad<S, Team::multi> xl{yprev, lo, hi};
               for (int r = lo + tid; r < hi; r += nth) V[(size_t)j * ld + r] = E::scale(yprev[r], sc);
-              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, stg, rpc));
+              PM_SPMV_OR_FAIL(spmv_rows<S>(P.A, xl, ycur, sc, true, lo, hi, stg));
             }
             matvecs += 1;
             kry_steps += 1;
