@@ -426,8 +426,12 @@ def run_batched(args, world, rank, local):
         X3, T3 = L.examples_every_step(traces)
         blob3, losses3 = L.train(solver, X3, T3, iters=3000, lr=3e-3)
         solver.set_controller_weights(blob3)
+        max_steps = solver.params.max_steps
+        solver.params.max_steps = 2000       # bounds the run if a trained network stalls a solve
         et_, est = measure(3)
+        solver.params.max_steps = max_steps
         every = {"value": world * count * args.steps / (sum(et_) / 1e3), "unit": "solves/s",
+                 "problems_not_ok": int(sum(1 for x in batch.statuses() if x != pm.OK)),
                  "examples": int(X3.shape[0]), "loss_last": float(losses3[-1]),
                  "rejects": int(sum(x["rejects"] for x in est)), "steps": int(sum(x["steps"] for x in est)),
                  "matvecs": int(sum(x["matvecs"] for x in est)),

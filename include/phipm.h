@@ -284,9 +284,12 @@ phipm_status phipm_trace_read(phipm_handle* h, phipm_trace_record* out, int64_t 
  * of the first step uses the proposal in place of Eq. (tau_0) and m_init (tau
  * ratio clamped to [1/32, 8] and to the interval, m to [1, m_max]); the error
  * estimate still accepts or rejects it, and the paper's controller handles every
- * later attempt and step.  With PHIPM_CTRL_LEARNED_STEPS the first attempt of
- * every step uses a proposal from the live state (same clamps); after a rejected
- * attempt the paper's controller takes over for the rest of the step.  The two
+ * later attempt and step.  With PHIPM_CTRL_LEARNED_STEPS the first step is
+ * proposed as above, and the first attempt of every later step takes Algorithm 4's
+ * proposal with its tau raised by the network's ratio clamped to [1, 2] (m stays
+ * Algorithm 4's; a lowering correction would compound, since Algorithm 3 grows tau
+ * at most 2x per step); after a rejected attempt the paper's controller takes over
+ * for the rest of the step.  The two
  * modes want networks trained on different labels (learned.py). */
 #define PHIPM_MLP_PARAMS 4866
 #define PHIPM_CONTROLLER_FLOATS (PHIPM_MLP_PARAMS + 20)

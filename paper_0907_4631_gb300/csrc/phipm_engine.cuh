@@ -91,6 +91,31 @@ __device__ __forceinline__ typename E::Red red_warp_sum(typename E::Red v) {
     return v;
   }
 }
+// The sum of PM_WARPS (16) partials p[q * stride], q < 16, by one warp: lanes 0..15 load
+// one each and four shuffle levels add them (fixed order, so deterministic), against a
+// chain of 16 dependent adds by one thread (each FP64 add about 65 cycles).  Every lane
+// of the warp must call it; lane 0 holds the total.
+template <class E>
+__device__ __forceinline__ typename E::Red red_sum16(const double* p, int stride) {
+  static_assert(PM_WARPS == 16, "one partial per lane of a half warp");
+  const int lane = threadIdx.x & 31;
+  typename E::Red v;
+  if (lane < PM_WARPS) memcpy(&v, p + lane * stride, sizeof(v));
+  else v = E::red_zero();
+#pragma unroll
+  for (int o = 8; o; o >>= 1) {
+    typename E::Red t;
+    if constexpr (E::kind == 0) {
+      t = __shfl_xor_sync(0xffffffffu, v, o);
+    } else {
+      t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+      t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    }
+    v = E::red_add(v, t);
+  }
+  return v;
+}
+
 template <class R>
 __device__ __forceinline__ void red_put(double* p, const R& r) {
   static_assert(sizeof(R) == sizeof(double), "a partial fills one 8-byte slot");
@@ -234,10 +259,9 @@ __device__ __forceinline__ void block_sum(PmShared& s, const double* v, int cnt,
     }
   }
   __syncthreads();
-  if (threadIdx.x < cnt) {
-    double a = 0.0;
-    for (int q = 0; q < PM_WARPS; ++q) a += s.red[q][threadIdx.x];
-    out[threadIdx.x] = a;
+  for (int k = warp; k < cnt; k += PM_WARPS) {
+    const double a = red_sum16<Elem<double>>(&s.red[0][k], 8);
+    if (lane == 0) out[k] = a;
   }
   __syncthreads();
 }
@@ -810,10 +834,9 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    typename E::Red t = E::red_zero();
-    for (int w = 0; w < PM_WARPS; ++w) t = E::red_add(t, red_get<typename E::Red>(&red[i * PM_WARPS + w]));
-    s.coef[i] = E::red_val(t);
+  for (int i = warp; i < nvec; i += PM_WARPS) {
+    const typename E::Red t = red_sum16<E>(&red[i * PM_WARPS], 1);
+    if (lane == 0) s.coef[i] = E::red_val(t);
   }
   __syncthreads();
 }
@@ -2005,14 +2028,13 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
               c.tau = fmin(c.tau * ratio, c.t_end - c.t);
               c.m = (int)fmin(fmax(rint(64.0 * mm), 1.0), (double)prm.m_max);
             } else {
-              // later steps start from Algorithm 4's measured proposal: the network only
-              // corrects it within tau / 2 .. 2 tau and Algorithm 3's m range [3m/4, 4m/3],
-              // so a biased proposal cannot compound from step to step
-              const double ratio = exp2(fmin(fmax(lr, -1.0), 1.0));
+              // later steps start from Algorithm 4's measured proposal, and the network may
+              // only raise its tau, up to 2 tau; m stays Algorithm 4's.  Algorithm 3 lets tau
+              // grow by at most 2x per step, so a network that lowered tau (or m, which
+              // Algorithm 4 mostly keeps) on every step would ratchet the step size down for
+              // good; a raised tau that fails is rejected and the paper's controller retries.
+              const double ratio = exp2(fmin(fmax(lr, 0.0), 1.0));
               c.tau = fmin(c.tau * ratio, c.t_end - c.t);
-              const int m0 = c.m;
-              const int mp = (int)rint(64.0 * mm);
-              c.m = min(min(max(max(mp, (3 * m0) / 4), 1), (4 * m0 + 2) / 3), prm.m_max);
             }
             c.source = 1;
           }
