@@ -2,8 +2,8 @@
 //
 //   double  FP64 storage and FP64 arithmetic (DFMA).
 //   float   FP32 storage; SpMV and updates in FP32 with FP32 accumulation;
-//           dot products of FP32 vectors accumulated exactly-ish as float
-//           pairs (the FP32 products are exact as hi + lo).
+//           dot products of FP32 vectors summed in FP32 over chunks of four
+//           products and accumulated across chunks as float pairs.
 //   df32    "float pair": x = hi + lo with |lo| <= ulp(hi)/2, 8 bytes, about
 //           48 significant bits.  Every product and sum runs on the FP32 pipe
 //           through error-free transforms: TwoProduct by FMA (x*y = p + e
@@ -51,6 +51,13 @@ __device__ __forceinline__ void f2_add_prod(F2Acc& a, df32 x, df32 y) {
   float s, t;
   ef_two_sum(a.hi, p, s, t);
   a.lo += t + e;
+  a.hi = s;
+}
+// a += q for an FP32 value q (TwoSum of the high parts)
+__device__ __forceinline__ void f2_add_float(F2Acc& a, float q) {
+  float s, t;
+  ef_two_sum(a.hi, q, s, t);
+  a.lo += t;
   a.hi = s;
 }
 __device__ __forceinline__ df32 f2_round(const F2Acc& a) {
@@ -123,6 +130,10 @@ template <> struct Elem<double> {
   __device__ static __forceinline__ Red red_zero() { return 0.0; }
   __device__ static __forceinline__ double red_val(const Red& a) { return a; }
   __device__ static __forceinline__ void dot(Acc& a, double x, double y) { a = fma(x, y, a); }
+  __device__ static __forceinline__ void dot4(Acc& a, const double* x, const double* y) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a = fma(x[k], y[k], a);
+  }
   __device__ static __forceinline__ double val(const Acc& a) { return a; }
   __device__ static __forceinline__ double from_d(double x) { return x; }
   __device__ static __forceinline__ double to_d(double x) { return x; }
@@ -142,6 +153,17 @@ template <> struct Elem<float> {
   __device__ static __forceinline__ Red red_zero() { return f2_zero(); }
   __device__ static __forceinline__ double red_val(const Red& a) { return f2_value(a); }
   __device__ static __forceinline__ void dot(Acc& a, float x, float y) { f2_add_prod(a, x, y); }
+  // four products summed by an FP32 multiply-add chain, the chunk added to the float
+  // pair by TwoSum: the sum is exact to about 4 u32 of sum |x_k y_k| (Higham's bound for
+  // recursive summation), the size of the FP32 basis's own rounding, at a quarter of the
+  // FP32 instructions of four exact products
+  __device__ static __forceinline__ void dot4(Acc& a, const float* x, const float* y) {
+    float q = x[0] * y[0];
+    q = fmaf(x[1], y[1], q);
+    q = fmaf(x[2], y[2], q);
+    q = fmaf(x[3], y[3], q);
+    f2_add_float(a, q);
+  }
   __device__ static __forceinline__ double val(const Acc& a) { return f2_value(a); }
   __device__ static __forceinline__ float from_d(double x) { return (float)x; }
   __device__ static __forceinline__ double to_d(float x) { return (double)x; }
@@ -161,6 +183,10 @@ template <> struct Elem<df32> {
   __device__ static __forceinline__ Red red_zero() { return f2_zero(); }
   __device__ static __forceinline__ double red_val(const Red& a) { return f2_value(a); }
   __device__ static __forceinline__ void dot(Acc& a, df32 x, df32 y) { f2_add_prod(a, x, y); }
+  __device__ static __forceinline__ void dot4(Acc& a, const df32* x, const df32* y) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f2_add_prod(a, x[k], y[k]);
+  }
   __device__ static __forceinline__ double val(const Acc& a) { return f2_value(a); }
   __device__ static __forceinline__ df32 from_d(double x) { return df_from_d(x); }
   __device__ static __forceinline__ double to_d(df32 x) { return df_to_d(x); }

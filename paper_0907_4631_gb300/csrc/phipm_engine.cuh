@@ -815,10 +815,7 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
 #pragma unroll
       for (int u = 0; u < NG; ++u) {
         Acc acc = E::zero();
-        if (i0 + u < nvec) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) E::dot(acc, vq[u].x[k], yq.x[k]);
-        }
+        if (i0 + u < nvec) E::dot4(acc, vq[u].x, yq.x);
         d[u] = red_warp_sum<E>(E::red_of(acc, E::zero()));
       }
       if (lane == 0) {
@@ -867,19 +864,25 @@ __device__ __forceinline__ typename Elem<S>::Red dot_segment(const S* __restrict
     v1.load(v + e + 128); y1.load(y + e + 128);
     v2.load(v + e + 256); y2.load(y + e + 256);
     v3.load(v + e + 384); y3.load(y + e + 384);
+    if constexpr (E::kind == 1) {
+      E::dot4(acc0, v0.x, y0.x);
+      E::dot4(acc1, v1.x, y1.x);
+      E::dot4(acc0, v2.x, y2.x);
+      E::dot4(acc1, v3.x, y3.x);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      E::dot(acc0, v0.x[k], y0.x[k]);
-      E::dot(acc1, v1.x[k], y1.x[k]);
-      E::dot(acc0, v2.x[k], y2.x[k]);
-      E::dot(acc1, v3.x[k], y3.x[k]);
+      for (int k = 0; k < 4; ++k) {
+        E::dot(acc0, v0.x[k], y0.x[k]);
+        E::dot(acc1, v1.x[k], y1.x[k]);
+        E::dot(acc0, v2.x[k], y2.x[k]);
+        E::dot(acc1, v3.x[k], y3.x[k]);
+      }
     }
   }
   for (; e + 3 < qb; e += 128) {
     Quad<S> v0, y0;
     v0.load(v + e); y0.load(y + e);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) E::dot(acc0, v0.x[k], y0.x[k]);
+    E::dot4(acc0, v0.x, y0.x);
   }
   if (qb + lane < b) E::dot(acc0, v[qb + lane], y[qb + lane]);      // tail: at most 3 rows
   return E::red_of(acc0, acc1);
@@ -1101,31 +1104,26 @@ __device__ __forceinline__ void dot_segment2(const S* __restrict__ v, const S* _
 #pragma unroll
       for (int u = 0; u < 4; ++u) { zq[u].load(z + e + 128 * u); wq[u].load(w + e + 128 * u); }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          E::dot((u & 1) ? z1 : z0, vq[u].x[k], zq[u].x[k]);
-          E::dot((u & 1) ? w1 : w0, vq[u].x[k], wq[u].x[k]);
-        }
+      for (int u = 0; u < 4; ++u) {
+        E::dot4((u & 1) ? z1 : z0, vq[u].x, zq[u].x);
+        E::dot4((u & 1) ? w1 : w0, vq[u].x, wq[u].x);
+      }
     }
   }
   for (; e + 128 + 3 < qb; e += 256) {        // two quads of each operand per lane in flight
     Quad<S> v0, v1, z0q, z1q, w0q, w1q;
     v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
     v1.load(v + e + 128); z1q.load(z + e + 128); w1q.load(w + e + 128);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      E::dot(z0, v0.x[k], z0q.x[k]);
-      E::dot(w0, v0.x[k], w0q.x[k]);
-      E::dot(z1, v1.x[k], z1q.x[k]);
-      E::dot(w1, v1.x[k], w1q.x[k]);
-    }
+    E::dot4(z0, v0.x, z0q.x);
+    E::dot4(w0, v0.x, w0q.x);
+    E::dot4(z1, v1.x, z1q.x);
+    E::dot4(w1, v1.x, w1q.x);
   }
   for (; e + 3 < qb; e += 128) {
     Quad<S> v0, z0q, w0q;
     v0.load(v + e); z0q.load(z + e); w0q.load(w + e);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { E::dot(z0, v0.x[k], z0q.x[k]); E::dot(w0, v0.x[k], w0q.x[k]); }
+    E::dot4(z0, v0.x, z0q.x);
+    E::dot4(w0, v0.x, w0q.x);
   }
   if (qb + lane < b) { E::dot(z0, v[qb + lane], z[qb + lane]); E::dot(w0, v[qb + lane], w[qb + lane]); }
   dz = E::red_of(z0, z1);
@@ -2544,7 +2542,17 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
           } else {
             F2Acc fa = f2_zero();
             if constexpr (E::kind == 1) {
-              for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucf[i], V[(size_t)i * ld + r]);
+              // chunks of four terms in FP32, the chunks summed as a float pair (the
+              // coefficients are FP32-rounded already, a relative error of u32 per term)
+              int i = 0;
+              for (; i + 3 < nvv; i += 4) {
+                float q = s.ucf[i] * V[(size_t)i * ld + r];
+                q = fmaf(s.ucf[i + 1], V[(size_t)(i + 1) * ld + r], q);
+                q = fmaf(s.ucf[i + 2], V[(size_t)(i + 2) * ld + r], q);
+                q = fmaf(s.ucf[i + 3], V[(size_t)(i + 3) * ld + r], q);
+                f2_add_float(fa, q);
+              }
+              for (; i < nvv; ++i) f2_add_prod(fa, s.ucf[i], V[(size_t)i * ld + r]);
             } else {
               for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucd[i], V[(size_t)i * ld + r]);
             }
