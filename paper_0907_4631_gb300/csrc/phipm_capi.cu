@@ -411,6 +411,12 @@ static DevOp make_devop(const phipm_operator* A, long long nnz_model) {
   return o;
 }
 
+// The four-row stencil product reads u (the caller's buffer, w_0 of the recurrence)
+// with 16-byte loads; a u that is only 8-byte aligned takes the one-row product.
+static void fit_quad_to_u(DevProblem& P) {
+  if (P.A.kind == 1 && (reinterpret_cast<uintptr_t>(P.u) & 15) != 0) P.A.quad = 0;
+}
+
 static long long round_ld(long long n) { return std::max(64ll, (n + 63) & ~63ll); }
 static size_t elem_bytes(int precision) { return precision == PHIPM_F32_MIXED ? 4 : 8; }
 
@@ -600,6 +606,7 @@ static phipm_status solve_impl(phipm_handle* h, int team_req, double t_end, cons
   P.tol = tol;
   for (int k = 0; k <= p; ++k) P.b[k] = b[k];
   P.u = u;
+  fit_quad_to_u(P);
   if (!assign_conversions(h, &P, 1, prec)) return fail(h, PHIPM_ENOMEM, "value conversion buffer");
   DevParams prm = make_params(h->params);
   st = attach_runtime(h, prm, stream);
@@ -798,6 +805,7 @@ extern "C" phipm_status phipm_solve_batched(phipm_handle* h, int32_t count, cons
       P.b[k] = b[i][k];
     }
     P.u = u[i];
+    fit_quad_to_u(P);
     nmax = std::max(nmax, n);
     pmax = std::max(pmax, (int)p[i]);
     cost[i] = (double)nnz_model + (double)n * 16.0;
@@ -1303,6 +1311,7 @@ extern "C" phipm_status phipm_solve_noalloc(double t_end, const phipm_operator* 
   P.tol = tol;
   for (int k = 0; k <= p; ++k) P.b[k] = b[k];
   P.u = u;
+  fit_quad_to_u(P);
   const DevParams prm = make_params(defaults);
   k_solve_noalloc<<<1, PM_THREADS, sizeof(PmShared), stream>>>(P, prm, scratch);
   if (cudaGetLastError() != cudaSuccess) return PHIPM_ECUDA;

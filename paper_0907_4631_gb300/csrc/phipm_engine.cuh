@@ -1431,6 +1431,141 @@ __device__ __noinline__ void update_rows2_cold(const S* V, long long ld, int nv,
 }
 
 // ------------------------------------------------------------------------------------
+// accept step (Eq. step) over this CTA's rows: udst = F + sum_{j<p} tau^j/j! w_j with
+// F = sum_{i<nvv} ucoef_i v_i (coefficients s.ucoef / s.ucf / s.ucd, the powers of tau
+// at s.ucoef[PM_NSLOT + j]).  Four rows per thread with 16-byte accesses when u and
+// udst allow them (the basis and W are 256-byte aligned, lo a multiple of 64 rows), so
+// that a thread has a quarter of the dependent load round trips; every row takes the
+// same operations in the same order as in the one-row form below.  Returns this
+// thread's sum of squares of the new rows when guard is set.
+// ------------------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ double accept_krylov_row(const S* __restrict__ V, long long ld, const PmShared& s, int nvv,
+                                                    int r) {
+  typedef Elem<S> E;
+  if constexpr (E::kind == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < nvv; ++i) acc = fma(s.ucoef[i], V[(size_t)i * ld + r], acc);
+    return acc;
+  } else {
+    F2Acc fa = f2_zero();
+    if constexpr (E::kind == 1) {
+      // chunks of four terms in FP32, the chunks summed as a float pair (the
+      // coefficients are FP32-rounded already, a relative error of u32 per term)
+      int i = 0;
+      for (; i + 3 < nvv; i += 4) {
+        float q = s.ucf[i] * V[(size_t)i * ld + r];
+        q = fmaf(s.ucf[i + 1], V[(size_t)(i + 1) * ld + r], q);
+        q = fmaf(s.ucf[i + 2], V[(size_t)(i + 2) * ld + r], q);
+        q = fmaf(s.ucf[i + 3], V[(size_t)(i + 3) * ld + r], q);
+        f2_add_float(fa, q);
+      }
+      for (; i < nvv; ++i) f2_add_prod(fa, s.ucf[i], V[(size_t)i * ld + r]);
+    } else {
+      for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucd[i], V[(size_t)i * ld + r]);
+    }
+    return f2_value(fa);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ double accept_rows(const S* __restrict__ V, long long ld, const PmShared& s, int nvv,
+                                              int p, const double* u, const double* __restrict__ W, double* udst,
+                                              bool guard, int lo, int hi) {
+  typedef Elem<S> E;
+  double un = 0.0;
+  int r0 = lo;
+  if (((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(udst)) & 15) == 0) {
+    const int nq = (hi - lo) >> 2;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      const int r = lo + 4 * q;
+      Quad<double> acc;
+      if constexpr (E::kind == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.x[k] = 0.0;
+        int i = 0;
+        for (; i + 1 < nvv; i += 2) {
+          Quad<double> v0, v1;
+          v0.load(V + (size_t)i * ld + r);
+          v1.load(V + (size_t)(i + 1) * ld + r);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc.x[k] = fma(s.ucoef[i], v0.x[k], acc.x[k]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc.x[k] = fma(s.ucoef[i + 1], v1.x[k], acc.x[k]);
+        }
+        if (i < nvv) {
+          Quad<double> v0;
+          v0.load(V + (size_t)i * ld + r);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc.x[k] = fma(s.ucoef[i], v0.x[k], acc.x[k]);
+        }
+      } else {
+        F2Acc fa[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fa[k] = f2_zero();
+        if constexpr (E::kind == 1) {
+          int i = 0;
+          for (; i + 3 < nvv; i += 4) {
+            Quad<float> v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) v[t].load(V + (size_t)(i + t) * ld + r);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              float c = s.ucf[i] * v[0].x[k];
+              c = fmaf(s.ucf[i + 1], v[1].x[k], c);
+              c = fmaf(s.ucf[i + 2], v[2].x[k], c);
+              c = fmaf(s.ucf[i + 3], v[3].x[k], c);
+              f2_add_float(fa[k], c);
+            }
+          }
+          for (; i < nvv; ++i) {
+            Quad<float> v0;
+            v0.load(V + (size_t)i * ld + r);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f2_add_prod(fa[k], s.ucf[i], v0.x[k]);
+          }
+        } else {
+          for (int i = 0; i < nvv; ++i) {
+            Quad<df32> v0;
+            v0.load(V + (size_t)i * ld + r);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f2_add_prod(fa[k], s.ucd[i], v0.x[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.x[k] = f2_value(fa[k]);
+      }
+      if (p >= 1) {
+        Quad<double> uq;
+        uq.load(u + r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.x[k] = fma(s.ucoef[PM_NSLOT], uq.x[k], acc.x[k]);
+      }
+      for (int jj = 1; jj < p; ++jj) {
+        Quad<double> wq;
+        wq.load(W + (size_t)(jj - 1) * ld + r);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc.x[k] = fma(s.ucoef[PM_NSLOT + jj], wq.x[k], acc.x[k]);
+      }
+      acc.store(udst + r);
+      if (guard) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) un = fma(acc.x[k], acc.x[k], un);
+      }
+    }
+    r0 = lo + 4 * nq;
+  }
+  for (int r = r0 + threadIdx.x; r < hi; r += blockDim.x) {
+    double acc = accept_krylov_row<S>(V, ld, s, nvv, r);
+    if (p >= 1) acc = fma(s.ucoef[PM_NSLOT], u[r], acc);
+    for (int jj = 1; jj < p; ++jj) acc = fma(s.ucoef[PM_NSLOT + jj], W[(size_t)(jj - 1) * ld + r], acc);
+    udst[r] = acc;
+    if (guard) un = fma(acc, acc, un);
+  }
+  return un;
+}
+
+// ------------------------------------------------------------------------------------
 // the exponential of the augmented matrix, spread over the team's CTAs
 // ------------------------------------------------------------------------------------
 #define PM_EXPM_MATS 13
@@ -2532,37 +2667,7 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
         // ||F|| / ||u_new|| can be bounded before it replaces u.
         const bool guard = (E::kind == 1) && p >= 2 && c.beta > 0.0;
         double* udst = guard ? ualt : u;
-        const int nvv = c.nvv;
-        double un = 0.0;
-        for (int r = lo + tid; r < hi; r += nth) {
-          double acc;
-          if constexpr (E::kind == 0) {
-            acc = 0.0;
-            for (int i = 0; i < nvv; ++i) acc = fma(s.ucoef[i], V[(size_t)i * ld + r], acc);
-          } else {
-            F2Acc fa = f2_zero();
-            if constexpr (E::kind == 1) {
-              // chunks of four terms in FP32, the chunks summed as a float pair (the
-              // coefficients are FP32-rounded already, a relative error of u32 per term)
-              int i = 0;
-              for (; i + 3 < nvv; i += 4) {
-                float q = s.ucf[i] * V[(size_t)i * ld + r];
-                q = fmaf(s.ucf[i + 1], V[(size_t)(i + 1) * ld + r], q);
-                q = fmaf(s.ucf[i + 2], V[(size_t)(i + 2) * ld + r], q);
-                q = fmaf(s.ucf[i + 3], V[(size_t)(i + 3) * ld + r], q);
-                f2_add_float(fa, q);
-              }
-              for (; i < nvv; ++i) f2_add_prod(fa, s.ucf[i], V[(size_t)i * ld + r]);
-            } else {
-              for (int i = 0; i < nvv; ++i) f2_add_prod(fa, s.ucd[i], V[(size_t)i * ld + r]);
-            }
-            acc = f2_value(fa);
-          }
-          if (p >= 1) acc = fma(s.ucoef[PM_NSLOT], u[r], acc);
-          for (int jj = 1; jj < p; ++jj) acc = fma(s.ucoef[PM_NSLOT + jj], W[(size_t)(jj - 1) * ld + r], acc);
-          udst[r] = acc;
-          if (guard) un = fma(acc, acc, un);
-        }
+        const double un = accept_rows<S>(V, ld, s, c.nvv, p, u, W, udst, guard, lo, hi);
         if (guard) {
           const double v[1] = {un};
           block_sum(s, v, 1, s.coef);

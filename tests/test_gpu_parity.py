@@ -351,3 +351,30 @@ def test_pade_exponential_option_matches_the_oracle(team):
         u, st = _gpu(s, pr)
         assert _rel(u, ref) <= TOL64
         assert st["steps"] == rst.steps
+
+
+@pytest.mark.parametrize("prec", ["f64", "f64pair", "f32"])
+@pytest.mark.parametrize("team", [1, 152])
+def test_output_only_eight_byte_aligned(prec, team):
+    """u at an 8-byte (not 16-byte) boundary, on a stencil whose side is a multiple of 4:
+    the library reads u as w_0 of the recurrence and writes every accepted step there, so
+    it takes the one-row stencil product and the one-row accept step; the result equals
+    the aligned solve's up to rounding (the two stencil forms add the neighbours in
+    different orders)."""
+    tol = TOL32 if prec == "f32" else 1e-8
+    pr = wl.laplacian_3d_problem(N=24, p=2, t_end=1e-4, tol=tol, seed=3124)
+    s = pm.Phipm(prec)
+    s.set_team(team)
+    A = pm.DeviceOperator(pr.op)
+    b = _dev(pr.b)
+    ua, sta, _ = s.solve(pr.t_end, A, b, pr.tol, 1)
+    buf = torch.empty(pr.n + 1, dtype=torch.float64, device="cuda")
+    uo = buf[1:]
+    assert uo.data_ptr() % 16 == 8
+    _, sto, _ = s.solve(pr.t_end, A, b, pr.tol, 1, out=uo)
+    torch.cuda.synchronize()
+    if prec == "f64":
+        assert sto["steps"] == sta["steps"]
+    assert _rel(uo.cpu().numpy(), ua.cpu().numpy()) <= {"f64": 1e-12, "f64pair": 1e-10, "f32": TOL32}[prec]
+    ref, _ = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 1)
+    assert _rel(uo.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
