@@ -173,6 +173,16 @@ typedef struct {
                              Stockmeyer) with scaling and squaring, no LU, faster on GB300.
                              Both are accurate to about the unit roundoff; the cost model of
                              Eq. (4) charges the Pade form either way. */
+  int32_t expm_action;    /* how the two columns phi_p(tau H) e1, phi_{p+1}(tau H) e1 of
+                             exp(H_hat) are formed.  0 (default): per attempt, as the action of
+                             exp(H_hat) on the two unit vectors (the degree-k Taylor polynomial
+                             of H_hat / s applied s times, k and s from ||H_hat||_1 with the same
+                             2^-53 tail bound; products of H_hat with vectors, upper Hessenberg
+                             or tridiagonal, each CTA on its own) where a cost estimate puts it
+                             below the full exponential with squarings, else the full
+                             exponential (expm_pade selects its form); 1: always the full
+                             exponential; 2: the action form whenever s <= 64.  With
+                             expm_pade = 1, mode 0 keeps the Pade exponential. */
 } phipm_params;
 
 /* Controllers.  PHIPM_CTRL_FIXED_M is the fixed-dimension variant the paper

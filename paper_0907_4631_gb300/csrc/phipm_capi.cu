@@ -139,6 +139,7 @@ extern "C" void phipm_default_params(phipm_params* o) {
   o->timeout_cycles = 20000000000ll;   // about 10 s at 2 GHz
   o->stencil_stage = 0;
   o->expm_pade = 0;
+  o->expm_action = 0;
 }
 
 static bool params_ok(const phipm_params& p, std::string& why) {
@@ -155,6 +156,7 @@ static bool params_ok(const phipm_params& p, std::string& why) {
   if (p.timeout_cycles <= 0) { why = "timeout_cycles must be positive"; return false; }
   if (p.stencil_stage != 0 && p.stencil_stage != 1) { why = "stencil_stage must be 0 or 1"; return false; }
   if (p.expm_pade != 0 && p.expm_pade != 1) { why = "expm_pade must be 0 or 1"; return false; }
+  if (p.expm_action < 0 || p.expm_action > 2) { why = "expm_action must be 0, 1 or 2"; return false; }
   return true;
 }
 
@@ -258,6 +260,46 @@ extern "C" phipm_status phipm_set_params(phipm_handle* h, const phipm_params* pa
 // ------------------------------------------------------------------------------------
 // helpers
 // ------------------------------------------------------------------------------------
+// theta(deg): the largest theta with sum_{k>deg} theta^k / k! <= 2^-53 e^-theta (the
+// truncated Taylor tail relative to the smallest possible |exp|), by bisection; for the
+// degree-18 squaring form and, as 1 / theta_k rounded up in FP32 (so that the steps
+// s = ceil(||H_hat|| / theta_k), formed in FP32 with a margin, never fall short), for the
+// action form's degrees k <= PM_XV_KMAX.  Computed once per process (every solve call
+// builds its parameter block).
+struct ThetaTables {
+  double theta18;
+  float itheta[PM_XV_KMAX + 1];
+  double inv_int[PM_XV_SMAX + 1];
+};
+static double theta_of(int deg) {
+  auto tail = [deg](double th) {
+    double term = 1.0, sum = 0.0;
+    for (int k = 1; k <= deg + 160; ++k) {
+      term *= th / (double)k;
+      if (k > deg) sum += term;
+    }
+    return sum;
+  };
+  double lo = 0.0, hi = (double)deg + 1.0;
+  for (int it = 0; it < 100; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (tail(mid) <= std::ldexp(1.0, -53) * std::exp(-mid)) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+static const ThetaTables& theta_tables() {
+  static const ThetaTables t = [] {
+    ThetaTables r;
+    r.theta18 = theta_of(18);
+    r.itheta[0] = 0.f;
+    for (int k = 1; k <= PM_XV_KMAX; ++k) r.itheta[k] = std::nextafter((float)(1.0 / theta_of(k)), INFINITY);
+    r.inv_int[0] = 0.0;
+    for (int j = 1; j <= PM_XV_SMAX; ++j) r.inv_int[j] = 1.0 / (double)j;
+    return r;
+  }();
+  return t;
+}
+
 static DevParams make_params(const phipm_params& p) {
   DevParams d;
   memset(&d, 0, sizeof(d));      // padding too: the batched form keys its captured graph on these bytes
@@ -286,28 +328,18 @@ static DevParams make_params(const phipm_params& p) {
     d.pade_b[j] = c;
     c = c * (double)(13 - j) / ((double)(26 - j) * (double)(j + 1));
   }
-  // degree-18 Taylor form: 1/k!, and the largest theta with sum_{k>18} theta^k / k! <=
-  // 2^-53 e^-theta (the truncated tail relative to the smallest possible |exp|), by bisection
+  // degree-18 Taylor form: 1/k!; its theta and the action form's from theta_tables()
   double f = 1.0;
   for (int k = 0; k <= 18; ++k) {
     d.taylor_c[k] = f;
     f /= (double)(k + 1);
   }
-  auto tail = [](double th) {
-    double term = 1.0, sum = 0.0;
-    for (int k = 1; k <= 60; ++k) {
-      term *= th / (double)k;
-      if (k > 18) sum += term;
-    }
-    return sum;
-  };
-  double lo = 0.0, hi = 4.0;
-  for (int it = 0; it < 80; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (tail(mid) <= std::ldexp(1.0, -53) * std::exp(-mid)) lo = mid; else hi = mid;
-  }
-  d.taylor_theta = lo;
+  const ThetaTables& tt = theta_tables();
+  d.taylor_theta = tt.theta18;
   d.expm_taylor = p.expm_pade ? 0 : 1;
+  d.expm_action = p.expm_action;
+  for (int k = 0; k <= PM_XV_KMAX; ++k) d.xv_itheta[k] = tt.itheta[k];
+  for (int j = 0; j <= PM_XV_SMAX; ++j) d.inv_int[j] = tt.inv_int[j];
   return d;
 }
 

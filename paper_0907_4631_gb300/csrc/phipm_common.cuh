@@ -10,6 +10,8 @@
 #define PM_MAXP 8
 #define PM_NA (PM_MAXM + PM_MAXP + 1)   // largest augmented matrix, Eq. (hathm) + 1
 #define PM_NA2 (PM_NA * PM_NA)
+#define PM_XV_KMAX 40                   // largest Taylor degree of the action form of exp(H_hat)
+#define PM_XV_SMAX 64                   // largest number of its steps
 #define PM_THREADS 512
 #define PM_WARPS (PM_THREADS / 32)
 #define PM_NSLOT 66                     // partial sums per reduction (j+1 <= 65, +1)
@@ -70,7 +72,9 @@ struct DevParams {
   double taylor_c[19];   // 1 / k!, k <= 18 (the Taylor exponential of multi-CTA teams)
   double taylor_theta;   // largest ||X||_1 for which the degree-18 Taylor truncation term is below 2^-53 e^-||X||
   int expm_taylor;       // 1: the exponential by the degree-18 Taylor form; 0: the degree-13 Pade form
-  int pad2;
+  int expm_action;       // 0: phi columns by the action form where it is estimated cheaper; 1: never; 2: always
+  float xv_itheta[PM_XV_KMAX + 1];   // 1 / theta_k of the action form's degree-k Taylor polynomial
+  double inv_int[PM_XV_SMAX + 1];    // 1 / j
   const float* mlp;      // learned-controller blob (device), or null
   TraceRec* trace;       // attempt records (device), or null
   unsigned long long* trace_count;

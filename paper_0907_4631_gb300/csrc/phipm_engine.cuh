@@ -34,6 +34,7 @@ struct PmScal {
   float invf;
   int m, m_used, kcur, invariant, sq, nonfinite, nvv, measure, outcome, status, go, symmetric, lanczos, last_m;
   int m_req, attempt, source, step_rejects, prev_rejects;
+  int xv_k, xv_s;                       // action form of this attempt's exponential (xv_s = 0: squaring form)
   long long steps, rejects, expms, trace_idx;
   float feat[MLP_IN];
 };
@@ -1730,6 +1731,124 @@ __device__ bool expm_taylor_team(const Team& team, PmShared& s, const double* tc
   return expm_square_out(team, s, cur, (cur == Y) ? Y2 : Y, out, N, m, sq, e0, e1, ca, cb);
 }
 
+// warps per SM sub-partition that threads 0 .. nthreads-1 fill (warp w runs on sub-partition w % 4)
+__device__ __forceinline__ int pm_warps_per_sp(int nthreads) { return ((nthreads + 31) / 32 + 3) / 4; }
+
+// The two columns ca, cb of exp(H_hat) without forming exp(H_hat): the action
+// F = exp(H_hat) [e_ca e_cb] as (T_k(H_hat / sd))^sd applied to the two unit vectors, T_k
+// the degree-k Taylor polynomial, with ||H_hat||_1 / sd <= theta_k, where theta_k bounds
+// the truncated tail by 2^-53 e^-theta_k as for the squaring form (the action route of
+// Al-Mohy and Higham, SIAM J. Sci. Comput. 33, 2011, with the forward tail bound).  The
+// products are H_hat times two N-vectors; H_hat is upper Hessenberg (tridiagonal when
+// tri, the Lanczos case) plus the unit entries of Eq. (hathm), so a step costs about
+// N m multiply-adds (3 N tridiagonal) against N^3 per matrix product.  On GB300 an FP64
+// warp instruction holds its SM sub-partition's FP64 pipe for about 64 cycles however
+// few lanes are active, so the outputs are spread one per thread over the first warps
+// (tridiagonal: one (row, vector) pair per thread, H_hat / sd as three diagonals and the
+// unit entries precomputed) or four lanes per row (Hessenberg: the lanes split the
+// columns of H, shuffle sum, each lane forming both vectors).  On return every thread
+// sees the top m entries of the columns in s.phi0 / s.phi1.
+static __device__ __noinline__ void expmv_cta(PmShared& s, const DevParams& prm, double tau, int m, int p, int ca,
+                                              int cb, int kdeg, int sd, bool tri) {
+  const int N = m + p + 1;
+  const int tid = threadIdx.x;
+  double* Bc = s.lu;                       // [2][PM_NA] current term
+  double* Bn = s.lu + 2 * PM_NA;           // [2][PM_NA] next term
+  double* F = s.lu + 4 * PM_NA;            // [2][PM_NA] partial sums
+  double* D = s.lu + 6 * PM_NA;            // tridiagonal: [4][PM_NA] sub, diagonal, super, unit entry (of H_hat / sd)
+  const double isd = prm.inv_int[sd];
+  for (int t = tid; t < 2 * PM_NA; t += blockDim.x) {
+    const int i = t % PM_NA;
+    const double v = (i == ((t < PM_NA) ? ca : cb)) ? 1.0 : 0.0;
+    Bc[t] = v;
+    F[t] = v;
+  }
+  if (tri) {
+    const double ts = tau * isd;
+    for (int i = tid; i < N; i += blockDim.x) {
+      const double* h = &s.H[i * PM_MAXM];
+      D[i] = (i < m && i > 0) ? ts * h[i - 1] : 0.0;
+      D[PM_NA + i] = (i < m) ? ts * h[i] : 0.0;
+      D[2 * PM_NA + i] = (i + 1 < m) ? ts * h[i + 1] : 0.0;
+      D[3 * PM_NA + i] = (i == 0 || (i >= m && i < m + p)) ? isd : 0.0;   // H_hat[0][m], H_hat[i][i+1]
+    }
+  }
+  __syncthreads();
+  constexpr int KS = 4;                    // lanes per dense row
+  const int L = (m + KS - 1) / KS;         // columns of H per lane
+  for (int st = 0; st < sd; ++st) {
+    for (int j = 1; j <= kdeg; ++j) {
+      const double ij = prm.inv_int[j];
+      if (tri) {
+        for (int t = tid; t < 2 * N; t += blockDim.x) {
+          const int col = (t < N) ? 0 : 1, i = t - col * N;
+          const double* b = Bc + col * PM_NA;
+          const int a = (i == 0) ? m : i + 1;                    // column of the unit entry of row i
+          double v = D[PM_NA + i] * b[i];
+          if (i > 0) v = fma(D[i], b[i - 1], v);
+          if (i + 1 < N) v = fma(D[2 * PM_NA + i], b[i + 1], v);
+          if (a < N) v = fma(D[3 * PM_NA + i], b[a], v);
+          v *= ij;
+          Bn[col * PM_NA + i] = v;
+          F[col * PM_NA + i] += v;
+        }
+      } else {
+        // N * KS <= 4 * 73 threads: every (row, lane) pair in one pass of a 512-thread CTA;
+        // whole warps take part (the shuffles), lanes past N * KS with zero sums
+        const double scale = isd * ij;
+        const int nt = (N * KS + 31) & ~31;
+        for (int t = tid; t < nt; t += blockDim.x) {
+          const bool act = t < N * KS;
+          const int i = t / KS, q = t - i * KS;
+          double a0 = 0.0, a1 = 0.0;
+          if (act && i < m) {
+            const int k0 = max(q * L, i - 1 > 0 ? i - 1 : 0), k1 = min(m, (q + 1) * L);
+            const double* h = &s.H[i * PM_MAXM];
+            for (int k = k0; k < k1; ++k) {
+              a0 = fma(h[k], Bc[k], a0);
+              a1 = fma(h[k], Bc[PM_NA + k], a1);
+            }
+          }
+          a0 += __shfl_xor_sync(0xffffffffu, a0, 1);
+          a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+          a0 += __shfl_xor_sync(0xffffffffu, a0, 2);
+          a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+          if (act && q == 0) {
+            double v0, v1;
+            if (i < m) {
+              v0 = tau * a0;
+              v1 = tau * a1;
+              if (i == 0) { v0 += Bc[m]; v1 += Bc[PM_NA + m]; }
+            } else {
+              v0 = (i < m + p) ? Bc[i + 1] : 0.0;
+              v1 = (i < m + p) ? Bc[PM_NA + i + 1] : 0.0;
+            }
+            v0 *= scale;
+            v1 *= scale;
+            Bn[i] = v0;
+            Bn[PM_NA + i] = v1;
+            F[i] += v0;
+            F[PM_NA + i] += v1;
+          }
+        }
+      }
+      __syncthreads();
+      double* t2 = Bc; Bc = Bn; Bn = t2;
+    }
+    // the next step starts from the partial sum: B = F
+    for (int t = tid; t < 2 * N; t += blockDim.x) {
+      const int o = (t < N) ? t : PM_NA + t - N;
+      Bc[o] = F[o];
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += blockDim.x) {
+    s.phi0[i] = F[i];
+    s.phi1[i] = F[PM_NA + i];
+  }
+  __syncthreads();
+}
+
 // exp(H_hat) with H_hat = [[tau H_m, e_1, 0], [0, 0, I_p], [0, 0, 0]] (Eq. hathm,
 // size N = m+p+1), degree-13 Pade approximant (even/odd split) with sq
 // squarings (Sec. 3.1).  Products are split over the team by elements; every CTA
@@ -2501,13 +2620,46 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
             c.hlast = (c.invariant && mu == c.kcur) ? 0.0 : s.H[mu * PM_MAXM + mu - 1];
             c.norm1 = fmax(mx, 1.0);
             c.sq = pm_squarings(c.norm1, prm.theta13);
+            // the action form's degree k and steps sd: the fewest products k sd with
+            // ||H_hat||_1 / sd <= theta_k, in FP32 with a margin (s rounds up); taken in mode
+            // 0 by one-CTA teams where its estimated cycles (k sd products of H_hat with two
+            // vectors) are below those of the squaring form's 7 + s matrix products (a
+            // multi-CTA team splits those products over its CTAs, the action form cannot)
+            c.xv_k = 0;
+            c.xv_s = 0;
+            if (prm.expm_action == 2 || (prm.expm_action == 0 && prm.expm_taylor && team.size() == 1)) {
+              const float nf = (float)c.norm1 * 1.0000005f;
+              int bk = 0, bs = 0, best = 1 << 30;
+              for (int k = 2; k <= PM_XV_KMAX; ++k) {
+                const float q = ceilf(nf * prm.xv_itheta[k]);
+                if (!(q <= (float)PM_XV_SMAX)) continue;
+                const int ss = max(1, (int)q);
+                if (k * ss < best) { best = k * ss; bk = k; bs = ss; }
+              }
+              bool take = bs > 0 && prm.expm_action == 2;
+              if (bs > 0 && prm.expm_action == 0) {
+                // cycles, counting FP64 warp instructions per sub-partition at 64 cycles
+                // each: a vector step (tridiagonal: 6 per output thread; Hessenberg: two
+                // multiply-adds per column of a lane's slice, 8 more) plus 250 for its
+                // barrier, against 7 + s products of N^3 multiply-adds at 2 per cycle
+                const int N = mu + p + 1;
+                const int wsp = pm_warps_per_sp(c.lanczos ? 2 * N : 4 * N);
+                const float per = 250.f + 64.f * (float)wsp * (c.lanczos ? 6.f : (float)(2 * ((mu + 3) / 4) + 8));
+                const float sqt = fmaxf(0.f, ceilf(log2f(nf / (float)prm.taylor_theta)));
+                const float Nf = (float)N;
+                take = (float)best * per < (7.f + sqt) * 0.5f * Nf * Nf * Nf;
+              }
+              if (take) { c.xv_k = bk; c.xv_s = bs; }
+            }
           }
         }
         __syncthreads();
         const int mu = c.m_used;
         const int ca = (p >= 1) ? mu + p - 1 : 0;
         const int cb = mu + p;
-        if (!expm_team(team, s, prm, c.norm1, c.tau_used, mu, p, c.sq, w.expm, ca, cb)) {
+        if (c.xv_s > 0) {
+          expmv_cta(s, prm, c.tau_used, mu, p, ca, cb, c.xv_k, c.xv_s, c.lanczos != 0);
+        } else if (!expm_team(team, s, prm, c.norm1, c.tau_used, mu, p, c.sq, w.expm, ca, cb)) {
           if (tid == 0) c.status = PM_ETIMEOUT;
           goto done;
         }

@@ -70,7 +70,8 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("delta", c_double), ("m_init", c_int32), ("m_max", c_int32),
                 ("theta13", c_double), ("breakdown_tol", c_double), ("max_steps", c_int64),
                 ("max_rejects", c_int64), ("precision", c_int32), ("controller", c_int32),
-                ("timeout_cycles", c_int64), ("stencil_stage", c_int32), ("expm_pade", c_int32)]
+                ("timeout_cycles", c_int64), ("stencil_stage", c_int32), ("expm_pade", c_int32),
+                ("expm_action", c_int32)]
 
 
 _LIB = None

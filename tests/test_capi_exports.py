@@ -75,6 +75,11 @@ def test_invalid_params_rejected_without_gpu():
     p.controller = pm.CTRL_LEARNED_STEPS + 1
     assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
     assert not h.value
+    for bad in (-1, 3):
+        p = pm.default_params()
+        p.expm_action = bad
+        assert L.phipm_create(ctypes.byref(h), ctypes.byref(p)) == pm.EINVAL
+        assert not h.value
 
 
 def test_tuning_entry_points_reject_null_handles(tmp_path):

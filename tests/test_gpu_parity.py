@@ -378,3 +378,38 @@ def test_output_only_eight_byte_aligned(prec, team):
     assert _rel(uo.cpu().numpy(), ua.cpu().numpy()) <= {"f64": 1e-12, "f64pair": 1e-10, "f32": TOL32}[prec]
     ref, _ = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 1)
     assert _rel(uo.cpu().numpy(), ref) <= (TOL32 if prec == "f32" else TOL64)
+
+
+@pytest.mark.parametrize("action", [0, 1, 2])
+@pytest.mark.parametrize("team", [1, 4, 152])
+@pytest.mark.parametrize("case", ["lanczos", "arnoldi"])
+def test_exponential_action_form_matches_the_oracle(action, team, case):
+    """params.expm_action: the phi columns from the action of exp(H_hat) on two unit vectors
+    (2), from the full exponential (1), or chosen per attempt by cost (0, the default);
+    tridiagonal (Lanczos) and Hessenberg (Arnoldi) H, one CTA, a cluster, the grid.  Each
+    meets the oracle (the exponential of the augmented matrix, Eq. hathm) with the same
+    steps, and the sine expansion in the symmetric case."""
+    if case == "lanczos":
+        pr = wl.laplacian_2d_problem()
+        ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 1)
+    else:
+        pr = wl.convdiff_2d_problem(N=130, p=3, t_end=1e-3, tol=1e-8, seed=2231)
+        ref, rst = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 0)
+    s = pm.Phipm("f64", expm_action=action)
+    s.set_team(team)
+    u, st = _gpu(s, pr)
+    assert _rel(u, ref) <= TOL64
+    assert st["steps"] == rst.steps and st["rejects"] == rst.rejects
+    if case == "lanczos":
+        assert _rel(u, T.solution_laplacian(2, 32, pr.b, pr.t_end)) <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["f64pair", "f32"])
+def test_exponential_action_form_other_precisions(prec):
+    tol = TOL32 if prec == "f32" else 1e-8
+    pr = wl.laplacian_3d_problem(N=24, p=2, t_end=1e-4, tol=tol, seed=3224)
+    ref, _ = O.phipm(pr.t_end, pr.op, pr.b, pr.tol, 1)
+    for action in (1, 2):
+        s = pm.Phipm(prec, expm_action=action)
+        u, _ = _gpu(s, pr)
+        assert _rel(u, ref) <= (TOL32 if prec == "f32" else TOL64)
