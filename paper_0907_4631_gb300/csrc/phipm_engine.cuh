@@ -789,6 +789,11 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
   for (int base = lo; base < hi; base += span) {
     const int r = base + 4 * threadIdx.x;
     const int nr = max(0, min(4, hi - r));   // rows of this thread in the tile
+    if (base + 128 * warp >= hi) {           // no rows for this warp: its partials are zero
+      if (base == lo && lane == 0)           // (skips the FP64 warp sums of small problems)
+        for (int i = 0; i < nvec; ++i) red_put(&red[i * PM_WARPS + warp], E::red_zero());
+      continue;
+    }
     Quad<S> yq;
     if (nr == 4) {
       yq.load(y + r);
@@ -815,9 +820,11 @@ __device__ void dots_rows(const S* __restrict__ V, long long ld, int nv, const S
       }
 #pragma unroll
       for (int u = 0; u < NG; ++u) {
-        Acc acc = E::zero();
-        if (i0 + u < nvec) E::dot4(acc, vq[u].x, yq.x);
-        d[u] = red_warp_sum<E>(E::red_of(acc, E::zero()));
+        if (i0 + u < nvec) {
+          Acc acc = E::zero();
+          E::dot4(acc, vq[u].x, yq.x);
+          d[u] = red_warp_sum<E>(E::red_of(acc, E::zero()));
+        }
       }
       if (lane == 0) {
 #pragma unroll
