@@ -26,6 +26,7 @@
 struct PmScal {
   double t, tau, tau_used, beta, eps, hlast, norm1, hn, inv, tol, t_end, normA, normb, bd_abs, err_sum;
   double fnorm, last_tau, omega, last_omega, m_new;
+  double tp;                            // tau^p of the accepted attempt
   double fz, fw, fab, dcoef;            // lagged Gram-Schmidt: z.z, z.w, a.b, d
   double fww, fbb;                      // w.w and ||b||^2 (first-pass retention of the next candidate)
   int skipz;                            // the current candidate keeps its single projection
@@ -2754,17 +2755,14 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
           c.m = m;
           if (omega <= prm.delta) {
             c.outcome = PM_ATT_ACCEPT;
-            // coefficients of Eq. (step) (a8) with F of Eq. (phipapprox2)
+            // coefficients of Eq. (step) (a8) with F of Eq. (phipapprox2): the corrector's
+            // here, the mu others (tp beta phi0[i]) by the whole CTA in the accept block
             const double tp = pow(tau_used, p);
+            c.tp = tp;
             int nvv = 0;
             if (c.beta > 0.0) {
-              for (int i = 0; i < mu; ++i) s.ucoef[i] = tp * c.beta * s.phi0[i];
               s.ucoef[mu] = (c.hlast != 0.0) ? tp * tau_used * c.beta * c.hlast * s.phi1[mu - 1] : 0.0;
               nvv = (s.ucoef[mu] != 0.0) ? mu + 1 : mu;
-              for (int i = 0; i < nvv; ++i) { s.ucf[i] = (float)s.ucoef[i]; s.ucd[i] = df_from_d(s.ucoef[i]); }
-              double fn = 0.0;     // ||F|| without the corrector (FP32 guard)
-              for (int i = 0; i < mu; ++i) fn = fma(s.phi0[i], s.phi0[i], fn);
-              c.fnorm = tp * c.beta * sqrt(fn);
             }
             c.nvv = nvv;
             double d = 1.0;
@@ -2825,6 +2823,24 @@ __device__ __forceinline__ void phipm_device(const Team& team, const DevProblem&
         // against the polynomial part; the candidate goes to a spare vector so that
         // ||F|| / ||u_new|| can be bounded before it replaces u.
         const bool guard = (E::kind == 1) && p >= 2 && c.beta > 0.0;
+        if (c.beta > 0.0) {
+          // the coefficients tp beta phi0[i] of F, i < mu, in FP64, FP32 and float pairs
+          const int mu = c.m_used, nvv = c.nvv;
+          const double tb = c.tp * c.beta;
+          for (int i = tid; i < nvv; i += nth) {
+            const double v = (i < mu) ? tb * s.phi0[i] : s.ucoef[i];
+            s.ucoef[i] = v;
+            s.ucf[i] = (float)v;
+            s.ucd[i] = df_from_d(v);
+          }
+          if (guard && tid < 32) {               // ||F|| without the corrector (FP32 guard)
+            double fn = 0.0;
+            for (int i = tid; i < mu; i += 32) fn = fma(s.phi0[i], s.phi0[i], fn);
+            fn = pm_warp_sum(fn);
+            if (tid == 0) c.fnorm = tb * sqrt(fn);
+          }
+          __syncthreads();
+        }
         double* udst = guard ? ualt : u;
         const double un = accept_rows<S>(V, ld, s, c.nvv, p, u, W, udst, guard, lo, hi);
         if (guard) {
