@@ -47,6 +47,24 @@ def test_noalloc_matches_oracle_and_phipm_solve_on_two_calls(N):
         assert stats["steps"] == ost.steps
 
 
+def test_noalloc_second_call_takes_no_device_memory():
+    """After the first call has loaded the module and its static array, a call with the
+    output preallocated leaves the device's free memory unchanged."""
+    pr = wl.convdiff_2d_problem(N=48, p=2, t_end=1e-3, tol=1e-8, seed=2990)
+    A = pm.DeviceOperator(pr.op)
+    b = _dev(pr.b)
+    u = torch.empty(pr.n, dtype=torch.float64, device="cuda")
+    _, _, st = pm.solve_noalloc(pr.t_end, A, b, pr.tol, 0, out=u)
+    torch.cuda.synchronize()
+    assert st == pm.OK
+    free0, _ = torch.cuda.mem_get_info()
+    _, _, st = pm.solve_noalloc(pr.t_end, A, b, pr.tol, 0, out=u)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert st == pm.OK
+    assert free1 == free0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = wl.laplacian(2, 91)                 # n = 8281 > 8192
     A = pm.DeviceOperator(st)
