@@ -270,6 +270,7 @@ struct ThetaTables {
   double theta18;
   float itheta[PM_XV_KMAX + 1];
   double inv_int[PM_XV_SMAX + 1];
+  double invfact[PM_XV_KMAX + 1];
 };
 static double theta_of(int deg) {
   auto tail = [deg](double th) {
@@ -295,6 +296,11 @@ static const ThetaTables& theta_tables() {
     for (int k = 1; k <= PM_XV_KMAX; ++k) r.itheta[k] = std::nextafter((float)(1.0 / theta_of(k)), INFINITY);
     r.inv_int[0] = 0.0;
     for (int j = 1; j <= PM_XV_SMAX; ++j) r.inv_int[j] = 1.0 / (double)j;
+    double f = 1.0;
+    for (int j = 0; j <= PM_XV_KMAX; ++j) {
+      r.invfact[j] = f;
+      f /= (double)(j + 1);
+    }
     return r;
   }();
   return t;
@@ -340,6 +346,7 @@ static DevParams make_params(const phipm_params& p) {
   d.expm_action = p.expm_action;
   for (int k = 0; k <= PM_XV_KMAX; ++k) d.xv_itheta[k] = tt.itheta[k];
   for (int j = 0; j <= PM_XV_SMAX; ++j) d.inv_int[j] = tt.inv_int[j];
+  for (int j = 0; j <= PM_XV_KMAX; ++j) d.xv_invfact[j] = tt.invfact[j];
   return d;
 }
 

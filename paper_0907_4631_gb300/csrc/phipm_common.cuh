@@ -75,6 +75,7 @@ struct DevParams {
   int expm_action;       // 0: phi columns by the action form where it is estimated cheaper; 1: never; 2: always
   float xv_itheta[PM_XV_KMAX + 1];   // 1 / theta_k of the action form's degree-k Taylor polynomial
   double inv_int[PM_XV_SMAX + 1];    // 1 / j
+  double xv_invfact[PM_XV_KMAX + 1]; // 1 / j!
   const float* mlp;      // learned-controller blob (device), or null
   TraceRec* trace;       // attempt records (device), or null
   unsigned long long* trace_count;

@@ -1758,101 +1758,110 @@ __device__ __forceinline__ int pm_warps_per_sp(int nthreads) { return ((nthreads
 // sees the top m entries of the columns in s.phi0 / s.phi1.
 static __device__ __noinline__ void expmv_cta(PmShared& s, const DevParams& prm, double tau, int m, int p, int ca,
                                               int cb, int kdeg, int sd, bool tri) {
+  // The terms are kept unscaled, Bt_j = (H_hat / sd)^j Bt_0, and enter the sum as
+  // F += Bt_j / j! (1/j! from the host): one FP64 multiply-add per output instead of a
+  // scaling and an add.  |Bt_j| <= theta_k^j |Bt_0| <= 6^40 |Bt_0| stays far inside the
+  // FP64 range.  Each output (row, vector) has one owning thread for the whole call
+  // (2N <= 146 tridiagonal, 4N <= 292 Hessenberg threads of the 512), which keeps its
+  // coefficients and its entry of F in registers.
   const int N = m + p + 1;
   const int tid = threadIdx.x;
   double* Bc = s.lu;                       // [2][PM_NA] current term
   double* Bn = s.lu + 2 * PM_NA;           // [2][PM_NA] next term
-  double* F = s.lu + 4 * PM_NA;            // [2][PM_NA] partial sums
-  double* D = s.lu + 6 * PM_NA;            // tridiagonal: [4][PM_NA] sub, diagonal, super, unit entry (of H_hat / sd)
   const double isd = prm.inv_int[sd];
   for (int t = tid; t < 2 * PM_NA; t += blockDim.x) {
     const int i = t % PM_NA;
-    const double v = (i == ((t < PM_NA) ? ca : cb)) ? 1.0 : 0.0;
-    Bc[t] = v;
-    F[t] = v;
+    Bc[t] = (i == ((t < PM_NA) ? ca : cb)) ? 1.0 : 0.0;
   }
-  if (tri) {
-    const double ts = tau * isd;
-    for (int i = tid; i < N; i += blockDim.x) {
-      const double* h = &s.H[i * PM_MAXM];
-      D[i] = (i < m && i > 0) ? ts * h[i - 1] : 0.0;
-      D[PM_NA + i] = (i < m) ? ts * h[i] : 0.0;
-      D[2 * PM_NA + i] = (i + 1 < m) ? ts * h[i + 1] : 0.0;
-      D[3 * PM_NA + i] = (i == 0 || (i >= m && i < m + p)) ? isd : 0.0;   // H_hat[0][m], H_hat[i][i+1]
-    }
-  }
-  __syncthreads();
   constexpr int KS = 4;                    // lanes per dense row
   const int L = (m + KS - 1) / KS;         // columns of H per lane
+  // this thread's output: tridiagonal (col, i) = (tid / N, tid % N); dense row i = tid / KS
+  // with lane q = tid % KS (lane 0 owns the outputs of both vectors)
+  const bool own_t = tri && tid < 2 * N;
+  const int tc = (tid < N) ? 0 : 1, ti = tid - tc * N;
+  const bool own_d = !tri && tid < N * KS;
+  const int di = tid / KS, dq = tid - di * KS;
+  double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;   // H_hat / sd: sub, diagonal, super, unit entry
+  int im = 0, ip = 0, ia = 0;                       // their columns (clamped into [0, N))
+  double f0 = 0.0, f1 = 0.0;                        // F entries owned (f1: second vector, dense lane 0)
+  if (own_t) {
+    const double ts = tau * isd;
+    const double* h = &s.H[ti * PM_MAXM];
+    d0 = (ti < m && ti > 0) ? ts * h[ti - 1] : 0.0;
+    d1 = (ti < m) ? ts * h[ti] : 0.0;
+    d2 = (ti + 1 < m) ? ts * h[ti + 1] : 0.0;
+    d3 = (ti == 0 || (ti >= m && ti < m + p)) ? isd : 0.0;   // H_hat[0][m], H_hat[i][i+1]
+    im = ti > 0 ? ti - 1 : 0;
+    ip = ti + 1 < N ? ti + 1 : ti;
+    const int a = (ti == 0) ? m : ti + 1;
+    ia = a < N ? a : ti;
+    f0 = (ti == (tc ? cb : ca)) ? 1.0 : 0.0;
+  }
+  if (own_d && dq == 0) {
+    f0 = (di == ca) ? 1.0 : 0.0;
+    f1 = (di == cb) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // dense: whole warps take part in the shuffles, lanes past N * KS with zero sums
+  const int nt = (N * KS + 31) & ~31;
   for (int st = 0; st < sd; ++st) {
     for (int j = 1; j <= kdeg; ++j) {
-      const double ij = prm.inv_int[j];
-      if (tri) {
-        for (int t = tid; t < 2 * N; t += blockDim.x) {
-          const int col = (t < N) ? 0 : 1, i = t - col * N;
-          const double* b = Bc + col * PM_NA;
-          const int a = (i == 0) ? m : i + 1;                    // column of the unit entry of row i
-          double v = D[PM_NA + i] * b[i];
-          if (i > 0) v = fma(D[i], b[i - 1], v);
-          if (i + 1 < N) v = fma(D[2 * PM_NA + i], b[i + 1], v);
-          if (a < N) v = fma(D[3 * PM_NA + i], b[a], v);
-          v *= ij;
-          Bn[col * PM_NA + i] = v;
-          F[col * PM_NA + i] += v;
+      const double cj = prm.xv_invfact[j];
+      if (own_t) {
+        const double* b = Bc + tc * PM_NA;
+        double v = d1 * b[ti];
+        v = fma(d0, b[im], v);
+        v = fma(d2, b[ip], v);
+        v = fma(d3, b[ia], v);
+        Bn[tc * PM_NA + ti] = v;
+        f0 = fma(cj, v, f0);
+      } else if (!tri && tid < nt) {
+        double a0 = 0.0, a1 = 0.0;
+        if (own_d && di < m) {
+          const int k0 = max(dq * L, di - 1 > 0 ? di - 1 : 0), k1 = min(m, (dq + 1) * L);
+          const double* h = &s.H[di * PM_MAXM];
+          for (int k = k0; k < k1; ++k) {
+            a0 = fma(h[k], Bc[k], a0);
+            a1 = fma(h[k], Bc[PM_NA + k], a1);
+          }
         }
-      } else {
-        // N * KS <= 4 * 73 threads: every (row, lane) pair in one pass of a 512-thread CTA;
-        // whole warps take part (the shuffles), lanes past N * KS with zero sums
-        const double scale = isd * ij;
-        const int nt = (N * KS + 31) & ~31;
-        for (int t = tid; t < nt; t += blockDim.x) {
-          const bool act = t < N * KS;
-          const int i = t / KS, q = t - i * KS;
-          double a0 = 0.0, a1 = 0.0;
-          if (act && i < m) {
-            const int k0 = max(q * L, i - 1 > 0 ? i - 1 : 0), k1 = min(m, (q + 1) * L);
-            const double* h = &s.H[i * PM_MAXM];
-            for (int k = k0; k < k1; ++k) {
-              a0 = fma(h[k], Bc[k], a0);
-              a1 = fma(h[k], Bc[PM_NA + k], a1);
-            }
+        a0 += __shfl_xor_sync(0xffffffffu, a0, 1);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+        a0 += __shfl_xor_sync(0xffffffffu, a0, 2);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+        if (own_d && dq == 0) {
+          double v0, v1;
+          if (di < m) {
+            v0 = tau * a0;
+            v1 = tau * a1;
+            if (di == 0) { v0 += Bc[m]; v1 += Bc[PM_NA + m]; }
+          } else {
+            v0 = (di < m + p) ? Bc[di + 1] : 0.0;
+            v1 = (di < m + p) ? Bc[PM_NA + di + 1] : 0.0;
           }
-          a0 += __shfl_xor_sync(0xffffffffu, a0, 1);
-          a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
-          a0 += __shfl_xor_sync(0xffffffffu, a0, 2);
-          a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
-          if (act && q == 0) {
-            double v0, v1;
-            if (i < m) {
-              v0 = tau * a0;
-              v1 = tau * a1;
-              if (i == 0) { v0 += Bc[m]; v1 += Bc[PM_NA + m]; }
-            } else {
-              v0 = (i < m + p) ? Bc[i + 1] : 0.0;
-              v1 = (i < m + p) ? Bc[PM_NA + i + 1] : 0.0;
-            }
-            v0 *= scale;
-            v1 *= scale;
-            Bn[i] = v0;
-            Bn[PM_NA + i] = v1;
-            F[i] += v0;
-            F[PM_NA + i] += v1;
-          }
+          v0 *= isd;
+          v1 *= isd;
+          Bn[di] = v0;
+          Bn[PM_NA + di] = v1;
+          f0 = fma(cj, v0, f0);
+          f1 = fma(cj, v1, f1);
         }
       }
       __syncthreads();
       double* t2 = Bc; Bc = Bn; Bn = t2;
     }
-    // the next step starts from the partial sum: B = F
-    for (int t = tid; t < 2 * N; t += blockDim.x) {
-      const int o = (t < N) ? t : PM_NA + t - N;
-      Bc[o] = F[o];
+    // the next step starts from the partial sum: Bt_0 = F
+    if (own_t) Bc[tc * PM_NA + ti] = f0;
+    if (own_d && dq == 0) {
+      Bc[di] = f0;
+      Bc[PM_NA + di] = f1;
     }
     __syncthreads();
   }
-  for (int i = tid; i < m; i += blockDim.x) {
-    s.phi0[i] = F[i];
-    s.phi1[i] = F[PM_NA + i];
+  if (own_t && ti < m) (tc ? s.phi1 : s.phi0)[ti] = f0;
+  if (own_d && dq == 0 && di < m) {
+    s.phi0[di] = f0;
+    s.phi1[di] = f1;
   }
   __syncthreads();
 }
