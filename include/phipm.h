@@ -52,7 +52,8 @@ typedef enum {
 typedef enum {
   PHIPM_F64 = 0,          /* basis, SpMV and all vector work in IEEE FP64 (FP64 pipe)        */
   PHIPM_F32_MIXED = 1,    /* basis and SpMV in FP32 with FP32 accumulation; Gram-Schmidt
-                             dot products accumulated as float pairs; coefficients, norms, H,
+                             dot products summed in FP32 over chunks of four products and
+                             accumulated across chunks as float pairs; coefficients, norms, H,
                              the exponential, eps and u in FP64                              */
   PHIPM_F64_PAIR = 2      /* FP64-class accuracy on the FP32 pipe: the basis is stored as
                              float pairs hi+lo (8 bytes, about 48 significant bits) and every
