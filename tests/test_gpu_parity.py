@@ -413,3 +413,25 @@ def test_exponential_action_form_other_precisions(prec):
         s = pm.Phipm(prec, expm_action=action)
         u, _ = _gpu(s, pr)
         assert _rel(u, ref) <= (TOL32 if prec == "f32" else TOL64)
+
+
+@pytest.mark.parametrize("p", [0, 1])
+@pytest.mark.parametrize("symm", [1, 0])
+def test_exponential_action_form_low_p(p, symm):
+    """The action form at p = 0 (H_hat's unit entry only in row 0) and p = 1, for the
+    tridiagonal (Lanczos) and Hessenberg (Arnoldi) H, one CTA, against the oracle."""
+    if symm:
+        A = wl.laplacian(2, 20)
+        b = [wl.normal(3300, k, A.n) for k in range(p + 1)]
+        t_end, tol = 2e-3, 1e-9
+        op = A
+    else:
+        pr = wl.convdiff_2d_problem(N=40, p=max(p, 1), t_end=1e-3, tol=1e-9, seed=3310)
+        op, b, t_end, tol = pr.op, pr.b[: p + 1], pr.t_end, pr.tol
+    ref, rst = O.phipm(t_end, op, b, tol, symm)
+    s = pm.Phipm("f64", expm_action=2)
+    s.set_team(1)
+    u, st, _ = s.solve(t_end, pm.DeviceOperator(op), _dev(b), tol, symm)
+    torch.cuda.synchronize()
+    assert _rel(u.cpu().numpy(), ref) <= TOL64
+    assert st["steps"] == rst.steps
